@@ -1,0 +1,69 @@
+/*
+ * FP64 oracle: the SVRG inner loop, written as plain loops.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Called (through ctypes) by oracle/lra_oracle.py,
+ * which is itself used only by the tests, the smoke check and the CPU baseline
+ * of the benchmark.  The library never links or calls this file.
+ *
+ * What it computes (Sec. 2.3 of the paper, SVRGsolve after Theorem 3): the
+ * linear system (lambda I - X X^T) W = B is the minimiser of
+ *     F(W) = 1/2 tr(W^T (lambda I - X X^T) W) - tr(B^T W)
+ *          = sum_i q_i f_i(W),  f_i(W) = 1/2 tr(W^T (lambda I - c_i x_i x_i^T) W) - tr(B^T W),
+ * with sampling probabilities q_i and c_i = 1/q_i.  Given the anchor Wt and the
+ * anchor gradient M = grad F(Wt) = lambda Wt - X X^T Wt - B, one variance-reduced
+ * step with sampled column i is
+ *     r = x_i^T (W - Wt)                                   (1 x p)
+ *     W <- W - eta [ lambda (W - Wt) - c_i x_i r + M ]
+ * i.e. grad f_i(W) - grad f_i(Wt) + grad F(Wt).  The p columns of W are
+ * independent chains that share the sampled index sequence.
+ *
+ * X is read exactly as stored (FP64, or FP32 widened element by element).
+ * Matrices are column-major: X is d x n with leading dimension ldx, W/Wt/M are
+ * d x p with leading dimension d.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+
+static void inner_loop(int64_t d, int64_t p, const double *Xd, const float *Xf, int64_t ldx,
+                       const int64_t *idx, int64_t m, const double *c, double eta,
+                       double lam, const double *Wt, const double *M, double *W)
+{
+    double *r = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t i = idx[t];
+        const double ci = c[i];
+        /* r_j = x_i^T (W_j - Wt_j) */
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = 0.0;
+            for (int64_t row = 0; row < d; ++row) {
+                const double x = Xd ? Xd[i * ldx + row] : (double)Xf[i * ldx + row];
+                acc += x * (W[j * d + row] - Wt[j * d + row]);
+            }
+            r[j] = acc;
+        }
+        /* W_j <- W_j - eta [ lambda (W_j - Wt_j) - c_i x_i r_j + M_j ] */
+        for (int64_t j = 0; j < p; ++j) {
+            for (int64_t row = 0; row < d; ++row) {
+                const double x = Xd ? Xd[i * ldx + row] : (double)Xf[i * ldx + row];
+                const double diff = W[j * d + row] - Wt[j * d + row];
+                const double g = lam * diff - ci * x * r[j] + M[j * d + row];
+                W[j * d + row] -= eta * g;
+            }
+        }
+    }
+    free(r);
+}
+
+void oracle_svrg_inner_f64(int64_t d, int64_t p, const double *X, int64_t ldx,
+                           const int64_t *idx, int64_t m, const double *c, double eta,
+                           double lam, const double *Wt, const double *M, double *W)
+{
+    inner_loop(d, p, X, NULL, ldx, idx, m, c, eta, lam, Wt, M, W);
+}
+
+void oracle_svrg_inner_f32(int64_t d, int64_t p, const float *X, int64_t ldx,
+                           const int64_t *idx, int64_t m, const double *c, double eta,
+                           double lam, const double *Wt, const double *M, double *W)
+{
+    inner_loop(d, p, NULL, X, ldx, idx, m, c, eta, lam, Wt, M, W);
+}
