@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-eps of the rank-k solve on one GB300 (and N replicas).
+
+A step is one complete lra_solve (lambda_1 estimate, shift, subspace iteration
+on (lambda I - X X^T)^-1 with SVRG solves, CholeskyQR2, Rayleigh-Ritz) on a
+synthetic planted-spectrum X resident in HBM.  The JSON line reports the mean
+device time per solve (CUDA events on the library's stream), the end-to-end
+time through the C ABI with host buffers, the roofline of the dominant kernel
+(from CUDA events around each of its launches), the SM clocks seen during the
+timed region, and the FP64 CPU oracle timed on a bounded sample.
+
+Multi-GPU: replicas only (each rank solves its own copy; no collective on the
+data path); the barrier and max-over-ranks timing follow the launch contract.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lra_inputs as L  # noqa: E402
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lra", "reference"], default="lra")
+    ap.add_argument("--workload", default="steep_head_4096x262144")
+    ap.add_argument("--storage", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--shift", choices=["far", "paper"], default="far")
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-outer", type=int, default=4)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# environment
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.close()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i - 5] for r in rows for i in range(5, 9) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def theory_rate(wl, lam):
+    s = wl.sigma()
+    lk, lp1 = s[wl.k - 1] ** 2, s[wl.p] ** 2
+    return ((lam - lk) / (lam - lp1)) ** 2
+
+
+def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
+    """Time the FP64 oracle on the same X and seeds: the lambda_1 estimate and
+    `outer_sample` outer iterations; returns (seconds for the fixed part,
+    seconds per outer iteration, the oracle's shift, its E trace)."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    from oracle import lra_oracle as O
+    X64 = np.asarray(Xt_host, dtype=np.float64)
+    pol = O.SHIFT_FAR if args.shift == "far" else O.SHIFT_PAPER
+    s = wl.sigma()
+    delta = (s[wl.k - 1] ** 2 - s[wl.p] ** 2) / 1.5
+    t0 = time.perf_counter()
+    ctx = O.Context(X64, args.seed, O.Options())
+    lh = O.lambda1_estimate(ctx)
+    t_fixed = time.perf_counter() - t0
+    o = O.Options(shift_policy=pol, delta=delta, min_outer=outer_sample, max_outer=outer_sample,
+                  tau=1e-5 if args.storage == "f32" else 1e-3)
+    t0 = time.perf_counter()
+    r = O.solve(X64, wl.k, wl.p, args.eps, args.seed, o, lam1_hat=lh)
+    t_outer = time.perf_counter() - t0
+    return t_fixed, t_outer / max(outer_sample, 1), r.lam, r.E_trace
+
+
+def predicted_outer(wl, lam, E_trace, eps):
+    """Outer iterations at which the stop rule fires, from the sampled Ritz
+    error and the asymptotic rate ((lambda - lambda_k)/(lambda - lambda_{p+1}))^2."""
+    opt = wl.opt()
+    r = theory_rate(wl, lam)
+    excess = max(E_trace[-1] - opt, 1e-300)
+    target = 0.25 * eps * opt
+    extra = max(0.0, math.log(target / excess) / math.log(r)) if excess > target else 0.0
+    return len(E_trace) - 1 + int(math.ceil(extra))
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def make_workload(args, device):
+    wl = L.WORKLOADS[args.workload]
+    import torch
+    Xt, U = L.planted_torch(wl.d, wl.n, wl.sigma(), wl.seed, device=device)
+    torch.cuda.synchronize()
+    return wl, Xt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    wl, Xt = make_workload(args, f"cuda:{local}")
+    Xh = Xt.cpu().numpy()
+    del Xt
+    torch.cuda.empty_cache()
+    threads = len(os.sched_getaffinity(0))
+    lam1 = None
+    vals = []
+    sample_desc = None
+    for i in range(args.warmup + args.steps):
+        t_fixed, t_outer, lam, E = oracle_sample(wl, Xh, args, lam1, args.cpu_sample_outer, threads)
+        Lstar = predicted_outer(wl, lam, E, args.eps)
+        v = t_fixed + t_outer * Lstar
+        sample_desc = (f"FP64 oracle on the same X and seeds: lambda_1 estimate + "
+                       f"{args.cpu_sample_outer} outer iterations, extrapolated to {Lstar} outer "
+                       f"iterations (sampled Ritz error, theory rate)")
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": "time-to-eps", "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
+                   "storage": args.storage, "shift": args.shift, "eps": args.eps},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_lra(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    import paper_1607_02925_gb300 as lra
+
+    wl, Xt = make_workload(args, device)
+    storage = lra.LRA_F32 if args.storage == "f32" else lra.LRA_BF16
+    esize = 4 if args.storage == "f32" else 2
+    s = wl.sigma()
+    delta = (s[wl.k - 1] ** 2 - s[wl.p] ** 2) / 1.5
+    pol = lra.LRA_SHIFT_FAR if args.shift == "far" else lra.LRA_SHIFT_PAPER
+    opt = lra.options(shift_policy=pol, delta=delta, profile=1)
+
+    ctx = lra.lra_init(local)
+    mat = lra.lra_create_dense(ctx, wl.d, wl.n, lra.LRA_F32, Xt, wl.d, True, storage)
+    stream = torch.cuda.ExternalStream(lra.lra_ctx_stream(ctx), device=device)
+    U = torch.zeros(wl.k, wl.d, dtype=torch.float32, device=device)
+    ritz = torch.zeros(wl.k, dtype=torch.float64, device=device)
+
+    def one(rep):
+        return lra.lra_solve(mat, wl.k, wl.p, args.eps, args.seed, opt, U, ritz, rep)
+
+    for _ in range(args.warmup):
+        one(lra.LraReport())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    reps = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rep = lra.LraReport()
+        st = one(rep)
+        reps.append((st, rep))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # accuracy of the last solve, off the clock (FP64, closed-form optimum)
+    Xd = Xt.double()
+    P = Xd @ U.double().T
+    fro2 = float((Xd * Xd).sum())
+    err = fro2 - float((P * P).sum())
+    ratio = err / wl.opt()
+    del Xd, P
+    torch.cuda.empty_cache()
+
+    # roofline of the dominant kernel from its live CUDA-event timing
+    peaks, peak_kind = measured_peaks()
+    last = reps[-1][1]
+    tot = {"xtw": sum(r.xtw_ms for _, r in reps), "xy": sum(r.xy_ms for _, r in reps),
+           "inner": sum(r.inner_ms for _, r in reps)}
+    cnt = {"xtw": sum(r.xtw_launches for _, r in reps), "xy": sum(r.xy_launches for _, r in reps),
+           "inner": sum(r.inner_launches for _, r in reps)}
+    cols = {"xtw": sum(r.xtw_cols for _, r in reps), "xy": sum(r.xy_cols for _, r in reps)}
+    dom = max(tot, key=lambda k: tot[k])
+    roof = None
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dom in ("xtw", "xy") and cnt[dom] > 0:
+        pav = cols[dom] / cnt[dom]
+        bytes_l = wl.d * wl.n * esize + (wl.d + wl.n) * pav * 4
+        flops_l = 2.0 * wl.d * wl.n * pav
+        t_l = tot[dom] / cnt[dom] / 1e3
+        hbm = peaks["hbm_gbs"] * 1e9
+        alu = 152 * 128 * 2 * sm_mhz * 1e6   # FP32 FMA lanes x 2 flop x clock
+        if bytes_l / hbm >= flops_l / alu:
+            roof = {"bound": "hbm", "achieved": bytes_l / t_l / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": bytes_l / t_l / hbm, "traffic": None}
+        else:
+            roof = {"bound": "alu", "achieved": flops_l / t_l / 1e12, "peak": alu / 1e12,
+                    "unit": "TFLOP/s", "frac": flops_l / t_l / alu, "traffic": None}
+        roof.update({"kernel": "xtw_kernel" if dom == "xtw" else "xy_kernel",
+                     "launches": cnt[dom], "ms_per_launch": t_l * 1e3,
+                     "algorithmic_bytes_per_launch": bytes_l,
+                     "x_pass_gbs": bytes_l / t_l / 1e9, "peak_source": peak_kind})
+    elif cnt["inner"] > 0:
+        roof = {"bound": "latency", "achieved": None, "peak": None, "unit": "steps/s",
+                "frac": None, "traffic": None, "kernel": "svrg_inner_kernel"}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty(Xt.shape, dtype=torch.float32, pin_memory=True)
+        Xh.copy_(Xt)
+        Uh = torch.empty(wl.k, wl.d, dtype=torch.float32, pin_memory=True)
+        rh = torch.empty(wl.k, dtype=torch.float64, pin_memory=True)
+        lra.lra_mat_destroy(mat)
+        mat = None
+        del Xt
+        torch.cuda.empty_cache()
+        times = []
+        for _ in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = lra.lra_create_dense(ctx, wl.d, wl.n, lra.LRA_F32, Xh, wl.d, False, storage)
+            lra.lra_solve(m2, wl.k, wl.p, args.eps, args.seed, opt, Uh, rh, lra.LraReport())
+            lra.lra_mat_destroy(m2)
+            times.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.mean(times[1:]), "unit": "s",
+               "h2d_bytes_per_step": wl.d * wl.n * 4,
+               "d2h_bytes_per_step": wl.d * wl.k * 4 + wl.k * 8}
+    else:
+        Xh = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = len(os.sched_getaffinity(0))
+        if Xh is None:
+            Xh = Xt.cpu()
+        t_fixed, t_outer, lam, E = oracle_sample(wl, Xh.numpy(), args, None, args.cpu_sample_outer, threads)
+        Lg = last.outer_iters
+        cpu = {"value": t_fixed + t_outer * Lg, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": (f"FP64 oracle on the same X and seeds: lambda_1 estimate ({t_fixed:.1f} s) "
+                          f"+ {args.cpu_sample_outer} outer iterations ({t_outer:.2f} s each), "
+                          f"extrapolated to the GPU run's {Lg} outer iterations")}
+
+    if mat is not None:
+        lra.lra_mat_destroy(mat)
+    lra.lra_finalize(ctx)
+    if rank == 0:
+        line = {
+            "metric": "time-to-eps", "value": ms_step / 1e3, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
+                       "storage": args.storage, "shift": args.shift, "eps": args.eps,
+                       "l2": "inputs larger than L2 (X %.2f GB per pass)" % (wl.d * wl.n * esize / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy": {"ratio_err_over_opt": ratio, "outer_iters": last.outer_iters,
+                         "status": reps[-1][0]},
+            "roofline": roof,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": int(sum(r.kernel_launches for _, r in reps)),
+            "kernel_ms": {k: v / args.steps for k, v in tot.items()},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lra(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -257,6 +257,8 @@ WORKLOADS = {
     "small_gap_256x2048": Workload("small_gap_256x2048", 256, 2048, 5, 10, 256, 0, "f64"),
     # FP32 dense, d=4096, n=262144, k=20, p=40
     "steep_head_4096x262144": Workload("steep_head_4096x262144", 4096, 262144, 20, 40, 4096, 2, "f32"),
+    # the same spectrum and d with n = 65536 (X = 1 GB): profiling captures
+    "steep_head_4096x65536": Workload("steep_head_4096x65536", 4096, 65536, 20, 40, 4096, 2, "f32"),
     # BF16 (and FP32) dense, d=8192, n=1048576, k=50, p=100
     "exp_two_gaps_8192x1048576": Workload("exp_two_gaps_8192x1048576", 8192, 1048576, 50, 100, 640, 3, "bf16"),
 }

@@ -1,0 +1,661 @@
+// The method's steps on the device (q = k branch of Algorithm 6):
+//   lambda_1 estimate (Algorithm 3, C = X X^T, k = 1), shift tuning
+//   (Algorithm 7), subspace iteration (Algorithm 1) on (lambda I - X X^T)^-1
+//   with SVRG solves (Sec. 2.3), CholeskyQR2, and Rayleigh-Ritz (Algorithm 2).
+// Host code only sequences kernels and reads back the few scalars that drive
+// control flow (residual norms, Ritz values).
+#include <chrono>
+#include <cstring>
+
+#include "engine.h"
+
+namespace lra {
+
+void *dev_alloc(lra_ctx *ctx, size_t bytes) {
+    if (ctx->budget) {
+        const size_t now = ctx->used.fetch_add(bytes) + bytes;
+        if (now > ctx->budget) {
+            ctx->used.fetch_sub(bytes);
+            set_error("device memory budget exceeded");
+            throw Error{LRA_ENOMEM};
+        }
+    } else {
+        ctx->used.fetch_add(bytes);
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        ctx->used.fetch_sub(bytes);
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        throw Error{LRA_ENOMEM};
+    }
+    return p;
+}
+
+void dev_free(lra_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    ctx->used.fetch_sub(bytes);
+}
+
+Opts read_opts(const lra_options *o, lra_dtype storage) {
+    Opts r;
+    if (o) {
+        if (o->struct_size < sizeof(lra_options)) {
+            set_error("lra_options.struct_size too small");
+            throw Error{LRA_EINVAL};
+        }
+        r.shift_policy = o->shift_policy;
+        r.lambda = o->lambda;
+        r.delta = o->delta;
+        r.theta_eta = o->theta_eta;
+        r.theta_m = o->theta_m;
+        r.tau = o->tau;
+        r.max_epochs = o->max_epochs;
+        r.m_max = o->m_max;
+        r.min_outer = o->min_outer;
+        r.max_outer = o->max_outer;
+        r.fixed_epochs = o->fixed_epochs;
+        r.sampling = o->sampling;
+        r.warm_start = o->warm_start;
+        r.max_shift_rounds = o->max_shift_rounds;
+        r.lambda1_hat = o->lambda1_hat;
+        r.trace_E = o->trace_E;
+        r.trace_cap = o->trace_cap;
+        r.profile = o->profile;
+    }
+    if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
+    if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
+        r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
+        r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0)) {
+        set_error("invalid lra_options field");
+        throw Error{LRA_EINVAL};
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+size_t workspace_bytes(int64_t dpad, int64_t n, int pmax) {
+    const int PP = pad_p(pmax);
+    const int nch = xy_chunks(dpad, n);
+    size_t b = 0;
+    b += 6 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U
+    b += sizeof(float) * dpad * PP;             // Wr
+    b += 2 * sizeof(float) * n * PP;            // Q Y
+    b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
+    b += sizeof(double) * (8 * pmax * pmax + gram_scratch(pmax) + dpad);
+    return b;
+}
+
+Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
+    : ctx(c), dpad(dpad_), n(n_), pmax(pmax_), PPmax(pad_p(pmax_)) {
+    try {
+        const size_t blk = (size_t)dpad * pmax;
+        S = alloc<float>(blk);
+        W = alloc<float>(blk);
+        Wt = alloc<float>(blk);
+        M = alloc<float>(blk);
+        T1 = alloc<float>(blk);
+        U = alloc<float>(blk);
+        Wr = alloc<float>((size_t)dpad * PPmax);
+        Q = alloc<float>((size_t)n * PPmax);
+        Y = alloc<float>((size_t)n * PPmax);
+        LRA_CUDA(cudaMemset(Q, 0, sizeof(float) * n * PPmax));
+        LRA_CUDA(cudaMemset(Y, 0, sizeof(float) * n * PPmax));
+        nchunks = xy_chunks(dpad, n);
+        Gp = alloc<float>((size_t)nchunks * dpad * PPmax);
+        const size_t pp = (size_t)pmax * pmax;
+        H = alloc<double>(pp);
+        evals = alloc<double>(pmax);
+        evecs = alloc<double>(pp);
+        eigwork = alloc<double>(sym_eig_work(pmax));
+        gscr = alloc<double>(gram_scratch(pmax));
+        Gm = alloc<double>(pp);
+        norms = alloc<double>(4);
+        epi = alloc<double>(2 * (dpad / 32) + 8);
+        dots = alloc<double>(pmax + 4);
+        Rinv = alloc<float>(pp);
+        P = alloc<float>(pp);
+        status = alloc<int>(4);
+        LRA_CUDA(cudaMallocHost(&host, sizeof(double) * (2 * pmax + 16)));
+    } catch (...) {
+        for (auto &a : allocs) dev_free(ctx, a.first, a.second);
+        allocs.clear();
+        throw;
+    }
+}
+
+Workspace::~Workspace() {
+    for (auto &a : allocs) dev_free(ctx, a.first, a.second);
+    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap);
+    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap);
+    if (host) cudaFreeHost(host);
+}
+
+void Workspace::ensure_idx(int64_t m) {
+    if (m <= idx_cap) return;
+    const int64_t cap = std::max<int64_t>(m, 2 * idx_cap);
+    cudaDeviceSynchronize();
+    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap);
+    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap);
+    idx = nullptr;
+    cval = nullptr;
+    idx_cap = 0;
+    idx = static_cast<int32_t *>(dev_alloc(ctx, sizeof(int32_t) * cap));
+    cval = static_cast<float *>(dev_alloc(ctx, sizeof(float) * cap));
+    idx_cap = cap;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel timer
+// ---------------------------------------------------------------------------
+KernelTimer::~KernelTimer() {
+    for (auto e : pool_) cudaEventDestroy(e);
+}
+
+size_t KernelTimer::event() {
+    if (used_ == pool_.size()) {
+        cudaEvent_t e;
+        LRA_CUDA(cudaEventCreate(&e));
+        pool_.push_back(e);
+    }
+    return used_++;
+}
+
+void KernelTimer::begin(Kind k, int cols) {
+    const size_t a = event();
+    LRA_CUDA(cudaEventRecord(pool_[a], s_));
+    recs_.push_back({(int)k, cols, a, a});
+}
+
+void KernelTimer::end() {
+    const size_t b = event();
+    LRA_CUDA(cudaEventRecord(pool_[b], s_));
+    recs_.back().e1 = b;
+}
+
+void KernelTimer::collect(double ms[3], int64_t launches[3], int64_t cols[3]) {
+    LRA_CUDA(cudaStreamSynchronize(s_));
+    for (int i = 0; i < 3; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+        cols[i] = 0;
+    }
+    for (const auto &r : recs_) {
+        float t = 0.0f;
+        LRA_CUDA(cudaEventElapsedTime(&t, pool_[r.e0], pool_[r.e1]));
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+        cols[r.kind] += r.cols;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+void Engine::sync() { LRA_CUDA(cudaStreamSynchronize(s_)); }
+
+void Engine::ensure_norms() {
+    std::lock_guard<std::mutex> g(mat_->setup_mu);
+    if (mat_->have_norms) return;
+    if (!mat_->norm2) {
+        mat_->norm2 = static_cast<double *>(dev_alloc(mat_->ctx, sizeof(double) * mat_->n));
+        mat_->dev_sm = static_cast<double *>(dev_alloc(mat_->ctx, sizeof(double) * 4));
+    }
+    colnorms(s_, mat_->X, mat_->storage, mat_->dpad, mat_->d, mat_->n, mat_->norm2);
+    sum_max(s_, mat_->norm2, mat_->n, mat_->dev_sm, nullptr);
+    double h[2];
+    LRA_CUDA(cudaMemcpyAsync(h, mat_->dev_sm, sizeof(h), cudaMemcpyDeviceToHost, s_));
+    sync();
+    mat_->fro2 = h[0];
+    mat_->maxn = h[1];
+    mat_->have_norms = true;
+}
+
+const lra_mat::Table &Engine::ensure_table(int mode) {
+    ensure_norms();
+    std::lock_guard<std::mutex> g(mat_->setup_mu);
+    auto &t = mat_->table[mode];
+    if (t.ok) return t;
+    const int64_t n = mat_->n;
+    if (!t.cum) {
+        t.cum = static_cast<uint64_t *>(dev_alloc(mat_->ctx, sizeof(uint64_t) * n));
+        t.c = static_cast<float *>(dev_alloc(mat_->ctx, sizeof(float) * n));
+    }
+    const int64_t scr = std::max<int64_t>(ceil_div(n, 1024) + 16, ceil_div(n, 256) + 16);
+    uint64_t *scratch = static_cast<uint64_t *>(dev_alloc(mat_->ctx, sizeof(uint64_t) * scr));
+    double *kap = reinterpret_cast<double *>(mat_->dev_sm) + 2;
+    try {
+        sampling_table(s_, mat_->norm2, n, mode, mat_->dev_sm + 1, t.cum, t.c, kap, scratch);
+        uint64_t tot = 0;
+        double kp = 0;
+        LRA_CUDA(cudaMemcpyAsync(&tot, t.cum + n - 1, sizeof(tot), cudaMemcpyDeviceToHost, s_));
+        LRA_CUDA(cudaMemcpyAsync(&kp, kap, sizeof(kp), cudaMemcpyDeviceToHost, s_));
+        sync();
+        t.total = tot;
+        t.kappa = kp;
+        t.ok = true;
+    } catch (...) {
+        cudaStreamSynchronize(s_);
+        dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr);
+        throw;
+    }
+    dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr);
+    if (t.total == 0) {
+        set_error("X has no non-zero column");
+        throw Error{LRA_EINVAL};
+    }
+    return t;
+}
+
+void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
+    const int PP = pad_p(p);
+    pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
+    if (timer) timer->begin(KernelTimer::XTW, p);
+    xtw(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, ws_.Wr, PP, Y);
+    if (timer) timer->end();
+    stats.x_passes += 1;
+}
+
+void Engine::x_mul(const float *Y, int p, float *G, bool use32) {
+    const int PP = pad_p(p);
+    if (timer) timer->begin(KernelTimer::XY, p);
+    xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y, PP, ws_.Gp, ws_.nchunks);
+    if (timer) timer->end();
+    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, PP, p, 0.0, nullptr, nullptr, G, nullptr,
+                    ws_.epi);
+    stats.x_passes += 1;
+}
+
+void Engine::a_apply(const float *W, int p, float *G) {
+    xt_mul(W, p, ws_.Y, false);
+    x_mul(ws_.Y, p, G, false);
+}
+
+void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *Y0,
+                    double *nM2, double *nB2) {
+    const int PP = pad_p(p);
+    const float *Y = Y0;
+    if (!Y) {
+        xt_mul(Wt, p, ws_.Y, false);
+        Y = ws_.Y;
+    }
+    if (timer) timer->begin(KernelTimer::XY, p);
+    xy(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, mat_->n, Y, PP, ws_.Gp, ws_.nchunks);
+    if (timer) timer->end();
+    stats.x_passes += 1;
+    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
+    if (nM2 || nB2) {
+        LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        sync();
+        if (nM2) *nM2 = ws_.host[0];
+        if (nB2) *nB2 = ws_.host[1];
+    }
+}
+
+void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
+                   const float *cval, int64_t m, double eta, double lam) {
+    if (timer) timer->begin(KernelTimer::INNER, p);
+    svrg_inner(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, p, W, Wt, M, idx, cval, m,
+               (float)eta, (float)lam);
+    if (timer) timer->end();
+}
+
+lra_status Engine::cholqr2(float *W, int p) {
+    const int64_t dpad = mat_->dpad;
+    LRA_CUDA(cudaMemsetAsync(ws_.status, 0, sizeof(int) * 2, s_));
+    for (int pass = 0; pass < 2; ++pass) {
+        gram(s_, W, dpad, 1, dpad, p, ws_.Gm, ws_.gscr);
+        chol_inv(s_, ws_.Gm, p, ws_.Rinv, ws_.status + pass);
+        apply_right(s_, W, dpad, 1, dpad, p, ws_.Rinv, p, ws_.T1, 1, dpad);
+        LRA_CUDA(cudaMemcpyAsync(W, ws_.T1, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
+    }
+    int st[2];
+    LRA_CUDA(cudaMemcpyAsync(st, ws_.status, sizeof(st), cudaMemcpyDeviceToHost, s_));
+    sync();
+    if (st[0] || st[1]) {
+        set_error("CholeskyQR2: Gram matrix not positive definite");
+        return LRA_ENUMERIC;
+    }
+    return LRA_OK;
+}
+
+void Engine::ritz(const float *S, int p, bool use32) {
+    const int PP = pad_p(p);
+    xt_mul(S, p, ws_.Q, use32);
+    gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
+    sym_eig(s_, ws_.H, p, ws_.evals, ws_.evecs, ws_.eigwork);
+}
+
+void Engine::normalize(float *z) {
+    col_dots(s_, z, z, mat_->dpad, mat_->dpad, 1, ws_.dots);
+    scale_cols_rsqrt(s_, z, mat_->dpad, mat_->dpad, 1, ws_.dots);
+}
+
+double Engine::dot1(const float *a, const float *b) {
+    col_dots(s_, a, b, mat_->dpad, mat_->dpad, 1, ws_.dots);
+    LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.dots, sizeof(double), cudaMemcpyDeviceToHost, s_));
+    sync();
+    return ws_.host[0];
+}
+
+void Engine::step_params(double lam, double mu, double l1up, double kappa, const Opts &o,
+                         double &eta, int64_t &m) const {
+    eta = o.theta_eta * mu / (lam * lam + kappa * l1up);
+    const double mm = std::ceil(o.theta_m / (eta * mu));
+    const int64_t m_max = o.m_max > 0 ? o.m_max : 50 * mat_->n;
+    m = (mm > (double)m_max) ? m_max : (int64_t)mm;
+}
+
+lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
+                              uint64_t seed, int64_t solve_id, const Opts &o, const float *Y0,
+                              SolveInfo &info) {
+    const auto &tab = ensure_table(o.sampling);
+    double eta;
+    int64_t m;
+    step_params(lam, mu, l1up, tab.kappa, o, eta, m);
+    info = SolveInfo();
+    info.m = m;
+    info.eta = eta;
+    stats.solves += 1;
+    const size_t blk = sizeof(float) * mat_->dpad * p;
+    const int max_e = o.fixed_epochs > 0 ? o.fixed_epochs : o.max_epochs;
+    double best = INFINITY, prev = INFINITY;
+    for (int e = 0; e < max_e; ++e) {
+        LRA_CUDA(cudaMemcpyAsync(ws_.Wt, W, blk, cudaMemcpyDeviceToDevice, s_));
+        double nM2, nB2;
+        anchor(ws_.Wt, B, p, lam, ws_.M, (e == 0) ? Y0 : nullptr, &nM2, &nB2);
+        stats.epochs += 1;
+        const double res = nB2 > 0 ? std::sqrt(nM2 / nB2) : 0.0;
+        info.epochs = e + 1;
+        info.residual = res;
+        if (!std::isfinite(res) || res > 10.0 * best) {
+            info.status = LRA_EDIVERGED;
+            return LRA_EDIVERGED;
+        }
+        if (o.fixed_epochs <= 0) {
+            if (res <= o.tau) return LRA_OK;
+            if (e >= 3 && res > 0.9 * prev) return LRA_OK;
+        }
+        if (e == max_e - 1) {
+            if (o.fixed_epochs <= 0) info.status = LRA_ENOTCONV;
+            return LRA_OK;
+        }
+        best = std::min(best, res);
+        prev = res;
+        ws_.ensure_idx(m);
+        const uint64_t key = stream_key(seed, LRA_STREAM_SVRG, (uint64_t)solve_id, (uint64_t)e);
+        sample(s_, tab.cum, mat_->n, key, m, ws_.idx, tab.c, ws_.cval);
+        inner(W, ws_.Wt, ws_.M, p, ws_.idx, ws_.cval, m, eta, lam);
+        info.inner_steps += m;
+        stats.inner_steps += m;
+    }
+    return LRA_OK;
+}
+
+double Engine::lambda1_estimate(uint64_t seed) {
+    const int64_t d = mat_->d;
+    const int L = (int)std::ceil(4.0 * std::log(4.0 * (double)d));
+    float *z = ws_.S;
+    gaussian(s_, stream_key(seed, LRA_STREAM_POWER_A, 0, 0), d, mat_->dpad, 1, z);
+    normalize(z);
+    for (int l = 0; l < L; ++l) {
+        a_apply(z, 1, ws_.W);
+        LRA_CUDA(cudaMemcpyAsync(z, ws_.W, sizeof(float) * mat_->dpad, cudaMemcpyDeviceToDevice, s_));
+        normalize(z);
+    }
+    xt_mul(z, 1, ws_.Y, false);
+    gram(s_, ws_.Y, mat_->n, pad_p(1), 1, 1, ws_.Gm, ws_.gscr);
+    LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.Gm, sizeof(double), cudaMemcpyDeviceToHost, s_));
+    sync();
+    return ws_.host[0];
+}
+
+lra_status Engine::d_top_inverse(uint64_t seed, int rnd, double lam, double mu, double l1up,
+                                 const Opts &o, int64_t &solve_count, double &inv) {
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    const int L = (int)std::ceil(9.0 * std::log(9.0 * (double)d));
+    float *z = ws_.S;
+    float *w = ws_.U;  // solve output (one column)
+    gaussian(s_, stream_key(seed, LRA_STREAM_POWER_D, (uint64_t)rnd, 0), d, dpad, 1, z);
+    normalize(z);
+    double scale = 1.0 / lam;
+    SolveInfo info;
+    for (int l = 0; l <= L; ++l) {
+        LRA_CUDA(cudaMemcpyAsync(w, z, sizeof(float) * dpad, cudaMemcpyDeviceToDevice, s_));
+        scale_block(s_, w, dpad, dpad, 1, (float)scale);
+        const lra_status st = svrg_solve(z, w, 1, lam, mu, l1up, seed, solve_count++, o, nullptr, info);
+        if (st != LRA_OK || info.status == LRA_EDIVERGED) return LRA_EDIVERGED;
+        if (l == L) {
+            const double lt = dot1(z, w);
+            if (!(lt > 0.0) || !std::isfinite(lt)) return LRA_EDIVERGED;
+            inv = 1.0 / lt;
+            return LRA_OK;
+        }
+        const double nw = std::sqrt(dot1(w, w));
+        if (!(nw > 0.0) || !std::isfinite(nw)) return LRA_EDIVERGED;
+        scale = nw;
+        LRA_CUDA(cudaMemcpyAsync(z, w, sizeof(float) * dpad, cudaMemcpyDeviceToDevice, s_));
+        normalize(z);
+    }
+    return LRA_OK;
+}
+
+lra_status Engine::shift_tune(uint64_t seed, double l1hat, double delta, const Opts &o,
+                              int64_t &solve_count, double &lam, double &inv, double &mu,
+                              int &rounds, std::vector<double> *history) {
+    const double eps = 1.0 / 9.0;
+    const double l1up = l1hat / (1.0 - 0.25);
+    lam = 1.5 * l1hat;
+    mu = lam - l1up;
+    inv = INFINITY;
+    rounds = 0;
+    for (int rnd = 0; rnd < o.max_shift_rounds; ++rnd) {
+        double est = 0.0;
+        const lra_status st = d_top_inverse(seed, rnd, lam, mu, l1up, o, solve_count, est);
+        rounds = rnd + 1;
+        if (history) {
+            history->push_back(lam);
+            history->push_back(est);
+        }
+        if (st != LRA_OK) return st;
+        inv = est;
+        if (delta / 27.0 <= est && est <= delta / 5.0) {
+            mu = (1.0 - eps) * est;
+            return LRA_OK;
+        }
+        lam = lam - 0.5 * (1.0 - eps) * est;
+        mu = 0.5 * (1.0 - eps) * est;
+    }
+    return LRA_ENOTCONV;
+}
+
+lra_status Engine::delta_estimate(int k, int p, uint64_t seed, double &delta) {
+    const int q = p + 1;
+    const int64_t d = mat_->d;
+    const double eps = 1.0 / (9.0 * p * p);
+    const int L = (int)std::min(200.0, std::ceil((1.0 / eps) * std::log((double)d / eps)));
+    float *S = ws_.S;
+    gaussian(s_, stream_key(seed, LRA_STREAM_DELTA, 0, 0), d, mat_->dpad, q, S);
+    lra_status st = cholqr2(S, q);
+    if (st != LRA_OK) return st;
+    for (int l = 0; l < L; ++l) {
+        a_apply(S, q, ws_.W);
+        LRA_CUDA(cudaMemcpyAsync(S, ws_.W, sizeof(float) * mat_->dpad * q, cudaMemcpyDeviceToDevice, s_));
+        st = cholqr2(S, q);
+        if (st != LRA_OK) return st;
+    }
+    ritz(S, q, false);
+    LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.evals, sizeof(double) * q, cudaMemcpyDeviceToHost, s_));
+    sync();
+    delta = (ws_.host[k - 1] - ws_.host[p]) / 1.5;
+    return LRA_OK;
+}
+
+static double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Stop rule of the outer loop: predicted remaining decrease of E_l
+// (r = clamp((E_{l-1}-E_l)/(E_{l-2}-E_{l-1}), 0, .99)) at most (eps/4) E_l.
+static bool outer_stop(const std::vector<double> &E, double eps, int ell, int min_outer) {
+    if (ell + 1 < std::max(3, min_outer)) return false;
+    const size_t n = E.size();
+    const double d1 = E[n - 2] - E[n - 1];
+    const double d0 = E[n - 3] - E[n - 2];
+    double r = d0 > 0 ? d1 / d0 : 0.99;
+    r = std::min(std::max(r, 0.0), 0.99);
+    const double remaining = std::max(d1, 0.0) * r / (1.0 - r);
+    return remaining <= 0.25 * eps * E[n - 1];
+}
+
+lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
+                         double *ritz_out, lra_report *rep, const std::atomic<int> *cancel) {
+    const auto t_all = std::chrono::steady_clock::now();
+    const int64_t launches0 = launches_of_thread();
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    std::unique_ptr<KernelTimer> own_timer;
+    if (o.profile) {
+        own_timer.reset(new KernelTimer(s_));
+        timer = own_timer.get();
+    }
+    lra_report R;
+    std::memset(&R, 0, sizeof(R));
+    R.struct_size = sizeof(R);
+    auto t0 = std::chrono::steady_clock::now();
+    const auto &tab = ensure_table(o.sampling);
+    (void)tab;
+    R.fro2 = mat_->fro2;
+    const double l1hat = o.lambda1_hat > 0 ? o.lambda1_hat : lambda1_estimate(seed);
+    const double l1up = l1hat / (1.0 - 0.25);
+    R.lambda1_hat = l1hat;
+    R.ms_setup = ms_since(t0);
+
+    t0 = std::chrono::steady_clock::now();
+    int64_t solve_count = 0;
+    double lam = 0, mu = 0, delta = o.delta;
+    lra_status status = LRA_OK;
+    if (o.shift_policy == LRA_SHIFT_PAPER) {
+        if (!(delta > 0)) {
+            status = delta_estimate(k, p, seed, delta);
+            if (status != LRA_OK) return status;
+        }
+        double inv = 0;
+        int rounds = 0;
+        status = shift_tune(seed, l1hat, delta, o, solve_count, lam, inv, mu, rounds, nullptr);
+        R.shift_rounds = rounds;
+        if (status == LRA_EDIVERGED) return status;
+        status = LRA_OK;  // a capped tuning still yields a valid shift > lambda_1
+    } else if (o.shift_policy == LRA_SHIFT_FAR) {
+        lam = 2.0 * l1up;
+        mu = lam - l1up;
+    } else {
+        lam = o.lambda;
+        mu = lam - l1up;
+        if (!(mu > 0)) {
+            set_error("FIXED shift must exceed lambda_hat_1 / (1 - 1/4)");
+            return LRA_EINVAL;
+        }
+    }
+    R.lambda = lam;
+    R.delta = delta;
+    R.mu_lb = mu;
+    R.ms_shift = ms_since(t0);
+
+    t0 = std::chrono::steady_clock::now();
+    float *S = ws_.S, *W = ws_.W;
+    gaussian(s_, stream_key(seed, LRA_STREAM_INIT, 0, 0), d, dpad, p, S);
+    lra_status st = cholqr2(S, p);
+    if (st != LRA_OK) return st;
+    std::vector<double> E;
+    int ell = 0;
+    const int PP = pad_p(p);
+    double *h = ws_.host;
+    while (true) {
+        ritz(S, p, false);
+        LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
+        sync();
+        double sk = 0.0;
+        for (int j = 0; j < k; ++j) sk += h[j];
+        E.push_back(mat_->fro2 - sk);
+        if (o.trace_E && (int)E.size() <= o.trace_cap) o.trace_E[E.size() - 1] = E.back();
+        if (outer_stop(E, eps, ell, o.min_outer)) break;
+        if (ell >= o.max_outer) {
+            status = LRA_ENOTCONV;
+            break;
+        }
+        if (cancel && cancel->load()) return LRA_ECANCELLED;
+        const float *Y0 = nullptr;
+        if (o.warm_start) {
+            ritz_inverse(s_, ws_.evecs, ws_.evals, p, lam, ws_.P);
+            apply_right(s_, S, dpad, 1, dpad, p, ws_.P, p, W, 1, dpad);
+            apply_right(s_, ws_.Q, mat_->n, PP, 1, p, ws_.P, p, ws_.Y, PP, 1);
+            Y0 = ws_.Y;
+        } else {
+            LRA_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * dpad * p, s_));
+        }
+        SolveInfo info;
+        st = svrg_solve(S, W, p, lam, mu, l1up, seed, solve_count++, o, Y0, info);
+        if (st != LRA_OK) return st;
+        R.eta = info.eta;
+        R.m = info.m;
+        R.last_residual = info.residual;
+        std::swap(S, W);
+        st = cholqr2(S, p);
+        if (st != LRA_OK) return st;
+        ++ell;
+    }
+    R.outer_iters = ell;
+    R.ms_outer = ms_since(t0);
+
+    t0 = std::chrono::steady_clock::now();
+    if (mat_->storage == LRA_BF16) {
+        // Algorithm 2 on the FP32 values of X: the answer is measured there
+        ritz(S, p, true);
+    }
+    evecs_to_rm(s_, ws_.evecs, p, k, ws_.P);
+    apply_right(s_, S, dpad, 1, dpad, p, ws_.P, k, ws_.U, 1, dpad);
+    LRA_CUDA(cudaMemcpy2DAsync(U, sizeof(float) * d, ws_.U, sizeof(float) * dpad, sizeof(float) * d, k,
+                               cudaMemcpyDefault, s_));
+    LRA_CUDA(cudaMemcpyAsync(ritz_out, ws_.evals, sizeof(double) * k, cudaMemcpyDefault, s_));
+    LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * k, cudaMemcpyDeviceToHost, s_));
+    sync();
+    {
+        double sk = 0.0;
+        for (int j = 0; j < k; ++j) sk += h[j];
+        R.err_est = mat_->fro2 - sk;
+    }
+    R.ms_final = ms_since(t0);
+    R.solves = stats.solves;
+    R.epochs = stats.epochs;
+    R.inner_steps = stats.inner_steps;
+    R.x_passes = stats.x_passes;
+    R.status = status;
+    R.kernel_launches = launches_of_thread() - launches0;
+    if (timer) {
+        double ms[3];
+        int64_t cnt[3], cols[3];
+        timer->collect(ms, cnt, cols);
+        R.xtw_ms = ms[0];
+        R.xy_ms = ms[1];
+        R.inner_ms = ms[2];
+        R.xtw_launches = cnt[0];
+        R.xy_launches = cnt[1];
+        R.inner_launches = cnt[2];
+        R.xtw_cols = cols[0];
+        R.xy_cols = cols[1];
+        timer = nullptr;
+    }
+    R.ms_total = ms_since(t_all);
+    if (rep) {
+        const size_t sz = std::min(rep->struct_size ? rep->struct_size : sizeof(R), sizeof(R));
+        std::memcpy(rep, &R, sz);
+        rep->struct_size = sz;
+    }
+    return status;
+}
+
+}  // namespace lra

@@ -1,0 +1,189 @@
+// Host-side objects of the library: contexts, matrices, per-solve workspaces
+// and the Engine that chains the kernels into the method's steps.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace lra {
+class Server;
+}
+
+struct lra_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;               // 0 = unlimited
+    std::atomic<size_t> used{0};     // device bytes allocated through this context
+    std::recursive_mutex mu;         // serialises step entry points and lra_solve
+    std::atomic<int> nmats{0};
+    std::unique_ptr<lra::Server> server;
+};
+
+struct lra_mat {
+    lra_ctx *ctx = nullptr;
+    int64_t d = 0, n = 0, dpad = 0;
+    lra_dtype storage = LRA_F32;
+    void *X = nullptr;     // storage dtype, dpad x n column-major
+    float *X32 = nullptr;  // FP32 copy (== X when storage is FP32)
+    // setup cache (a0)
+    std::mutex setup_mu;
+    bool have_norms = false;
+    double *norm2 = nullptr;  // device, n
+    double fro2 = 0.0, maxn = 0.0;
+    double *dev_sm = nullptr;  // device [sum, max]
+    struct Table {
+        bool ok = false;
+        uint64_t *cum = nullptr;
+        float *c = nullptr;
+        uint64_t total = 0;
+        double kappa = 0.0;
+    } table[2];
+    std::atomic<int> busy{0};
+};
+
+namespace lra {
+
+// Device allocation charged to a context's budget.
+void *dev_alloc(lra_ctx *ctx, size_t bytes);
+void dev_free(lra_ctx *ctx, void *p, size_t bytes);
+
+struct Opts {
+    int shift_policy = LRA_SHIFT_PAPER;
+    double lambda = 0.0, delta = 0.0;
+    double theta_eta = 0.25, theta_m = 2.0, tau = 0.0;
+    int max_epochs = 60;
+    int64_t m_max = 0;
+    int min_outer = 3, max_outer = 2000, fixed_epochs = 0;
+    int sampling = LRA_SAMPLE_IMPORTANCE, warm_start = 1, max_shift_rounds = 30;
+    double lambda1_hat = 0.0;
+    double *trace_E = nullptr;
+    int trace_cap = 0;
+    int profile = 0;
+};
+
+// CUDA-event timing of individual kernel launches on the engine's stream.
+class KernelTimer {
+   public:
+    enum Kind { XTW = 0, XY = 1, INNER = 2 };
+    explicit KernelTimer(cudaStream_t s) : s_(s) {}
+    ~KernelTimer();
+    void begin(Kind k, int cols);
+    void end();
+    // summed milliseconds, launch counts and processed columns per kind
+    void collect(double ms[3], int64_t launches[3], int64_t cols[3]);
+
+   private:
+    size_t event();
+    struct Rec {
+        int kind, cols;
+        size_t e0, e1;
+    };
+    cudaStream_t s_;
+    std::vector<cudaEvent_t> pool_;
+    size_t used_ = 0;
+    std::vector<Rec> recs_;
+};
+Opts read_opts(const lra_options *o, lra_dtype storage);
+
+struct SolveInfo {
+    int epochs = 0;
+    int64_t inner_steps = 0;
+    int64_t m = 0;
+    double eta = 0.0;
+    double residual = NAN;
+    lra_status status = LRA_OK;
+};
+
+struct Stats {
+    int64_t solves = 0, epochs = 0, inner_steps = 0, x_passes = 0;
+};
+
+// Per-solve buffers on the device, sized for up to pmax columns.
+struct Workspace {
+    lra_ctx *ctx = nullptr;
+    int64_t dpad = 0, n = 0;
+    int pmax = 0, PPmax = 0;
+    float *S = nullptr, *W = nullptr, *Wt = nullptr, *M = nullptr, *T1 = nullptr, *U = nullptr;
+    float *Wr = nullptr, *Q = nullptr, *Y = nullptr, *Gp = nullptr;
+    int nchunks = 0;
+    double *H = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
+    double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
+    float *Rinv = nullptr, *P = nullptr;
+    int *status = nullptr;
+    int32_t *idx = nullptr;
+    float *cval = nullptr;
+    int64_t idx_cap = 0;
+    double *host = nullptr;  // pinned readback area
+    std::vector<std::pair<void *, size_t>> allocs;
+
+    Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_);
+    ~Workspace();
+    void ensure_idx(int64_t m);
+    template <typename T>
+    T *alloc(size_t count) {
+        const size_t bytes = std::max<size_t>(16, sizeof(T) * count);
+        void *p = dev_alloc(ctx, bytes);
+        allocs.emplace_back(p, bytes);
+        return static_cast<T *>(p);
+    }
+};
+
+size_t workspace_bytes(int64_t dpad, int64_t n, int pmax);
+
+class Engine {
+   public:
+    Engine(lra_mat *mat, Workspace &ws, cudaStream_t s) : mat_(mat), ws_(ws), s_(s) {}
+
+    // a0 setup
+    void ensure_norms();
+    const lra_mat::Table &ensure_table(int mode);
+
+    // X products on p columns (internal padded layouts)
+    void xt_mul(const float *W, int p, float *Y, bool use32);            // Y n x PP rm
+    void x_mul(const float *Y, int p, float *G, bool use32);             // G dpad x p
+    void a_apply(const float *W, int p, float *G);                       // G = X X^T W
+    void anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *Y0,
+                double *nM2, double *nB2);
+    void inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
+               const float *cval, int64_t m, double eta, double lam);
+    lra_status cholqr2(float *W, int p);
+    void ritz(const float *S, int p, bool use32);  // -> ws.Q, ws.H, ws.evals, ws.evecs
+    void normalize(float *z);                      // one column, in place
+    double dot1(const float *a, const float *b);   // host read
+
+    void step_params(double lam, double mu, double l1up, double kappa, const Opts &o, double &eta,
+                     int64_t &m) const;
+    lra_status svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
+                          uint64_t seed, int64_t solve_id, const Opts &o, const float *Y0,
+                          SolveInfo &info);
+    double lambda1_estimate(uint64_t seed);
+    lra_status d_top_inverse(uint64_t seed, int rnd, double lam, double mu, double l1up,
+                             const Opts &o, int64_t &solve_count, double &inv);
+    lra_status shift_tune(uint64_t seed, double l1hat, double delta, const Opts &o,
+                          int64_t &solve_count, double &lam, double &inv, double &mu, int &rounds,
+                          std::vector<double> *history);
+    lra_status delta_estimate(int k, int p, uint64_t seed, double &delta);
+    lra_status solve(int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
+                     double *ritz, lra_report *rep, const std::atomic<int> *cancel);
+
+    void sync();
+    Stats stats;
+    KernelTimer *timer = nullptr;
+
+   private:
+    const void *xptr(bool use32) const { return use32 ? (const void *)mat_->X32 : mat_->X; }
+    lra_dtype xdt(bool use32) const { return use32 ? LRA_F32 : mat_->storage; }
+    lra_mat *mat_;
+    Workspace &ws_;
+    cudaStream_t s_;
+};
+
+}  // namespace lra

@@ -1,0 +1,226 @@
+// SVRG inner loop (Sec. 2.3, SVRGsolve): m serial variance-reduced steps
+//   r = x_i^T (W - Wt),  W <- W - eta [lambda (W - Wt) - c_i x_i r + M]
+// on the p columns of W, which are independent chains sharing the sampled
+// index sequence.  One CTA owns PC columns and the whole d-long state of each:
+// the difference Delta = W - Wt and the anchor gradient M live in registers,
+// the sampled columns x_i stream through a 4-deep shared-memory ring filled by
+// cp.async three steps ahead (the index sequence is known in advance), and
+// x_i^T Delta is reduced with warp shuffles and one barrier per step.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace lra {
+
+namespace {
+
+constexpr int kRing = 4;
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_bytes(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Thread t owns rows 4 (t + s NT) + v for s < S, v < 4 (rows >= dpad skipped).
+template <typename TX, int S, int PC>
+__global__ void __launch_bounds__(512) svrg_inner_kernel(
+    const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
+    const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
+    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [kRing][dpad]
+    __shared__ float red[2][16][PC];
+
+    const int tid = threadIdx.x;
+    const int NT = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+    const int j0 = blockIdx.x * PC;
+    constexpr int BYTES = 4 * sizeof(TX);
+
+    float dl[S][4][PC];   // Delta = W - Wt
+    float mm[S][4][PC];   // eta * M
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            const bool ok = (r < dpad) && (j0 + j < p);
+            const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                dl[s][v][j] = ok ? (W[off + v] - Wt[off + v]) : 0.0f;
+                mm[s][v][j] = ok ? eta * M[off + v] : 0.0f;
+            }
+        }
+    }
+
+    auto prefetch = [&](int64_t t) {
+        if (t < m) {
+            const int64_t i = idx[t];
+            const TX *col = X + i * ldx;
+            TX *slot = ring + (t & (kRing - 1)) * dpad;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+            }
+        }
+        cp_async_commit();
+    };
+
+    prefetch(0);
+    prefetch(1);
+    prefetch(2);
+    const float a = 1.0f - eta * lam;
+
+    for (int64_t t = 0; t < m; ++t) {
+        prefetch(t + 3);
+        cp_async_wait<3>();
+        const TX *slot = ring + (t & (kRing - 1)) * dpad;
+        float x[S][4];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+            if (r < dpad) {
+                if constexpr (sizeof(TX) == 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
+                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
+                } else {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
+            }
+        }
+        const float ci = cval[t];
+        float part[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
+            part[j] = warp_sum(acc);
+        }
+        const int buf = (int)(t & 1);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
+        }
+        __syncthreads();
+        float coef[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float rj = 0.0f;
+            for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
+            coef[j] = eta * ci * rj;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int j = 0; j < PC; ++j)
+                    dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(coef[j], x[s][v], -mm[s][v][j]));
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            if (r < dpad && j0 + j < p) {
+                const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) W[off + v] = Wt[off + v] + dl[s][v][j];
+            }
+        }
+    }
+}
+
+template <typename TX, int S, int PC>
+void launch_inner(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
+                  const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
+                  float eta, float lam, int nt) {
+    auto k = svrg_inner_kernel<TX, S, PC>;
+    const size_t smem = (size_t)kRing * dpad * sizeof(TX);
+    LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)ceil_div(p, PC);
+    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    LRA_LAUNCHED();
+}
+
+template <typename TX>
+constexpr size_t dt_size() { return sizeof(TX); }
+
+template <typename TX>
+void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
+                    const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
+                    float eta, float lam) {
+    // threads: 4 rows each, at most 512; S = row groups per thread
+    const int64_t groups = dpad / 4;
+    int nt = (int)std::min<int64_t>(512, round_up(groups, 32));
+    const int64_t S = ceil_div(groups, nt);
+    // columns per CTA: keep about <= 64 CTAs streaming the same x_i, and the
+    // register state (8 S PC floats) within 64 registers
+    const int pc = (p <= 64 || S > 4) ? 1 : 2;
+    if ((size_t)kRing * dpad * (dt_size<TX>()) > 220 * 1024) {
+        set_error("dense inner loop: d too large for the shared-memory ring");
+        throw Error{LRA_EUNSUPPORTED};
+    }
+#define LRA_INNER_CASE(SS, PCC)                                                                 \
+    if (S == SS && pc == PCC) {                                                                 \
+        launch_inner<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt); \
+        return;                                                                                 \
+    }
+    LRA_INNER_CASE(1, 1)
+    LRA_INNER_CASE(1, 2)
+    LRA_INNER_CASE(2, 1)
+    LRA_INNER_CASE(2, 2)
+    LRA_INNER_CASE(3, 1)
+    LRA_INNER_CASE(3, 2)
+    LRA_INNER_CASE(4, 1)
+    LRA_INNER_CASE(4, 2)
+    LRA_INNER_CASE(6, 1)
+    LRA_INNER_CASE(8, 1)
+#undef LRA_INNER_CASE
+    if (S <= 8) {
+        // S in {5, 7}: round up to the next instantiated size
+        if (S <= 6)
+            launch_inner<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+        else
+            launch_inner<TX, 8, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+        return;
+    }
+    set_error("dense inner loop supports d <= 16384");
+    throw Error{LRA_EUNSUPPORTED};
+}
+
+}  // namespace
+
+void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
+                float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
+                int64_t m, float eta, float lam) {
+    if (m <= 0) return;  // an empty step sequence leaves W unchanged
+    if (dt == LRA_BF16)
+        inner_dispatch<__nv_bfloat16>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    else
+        inner_dispatch<float>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+}
+
+}  // namespace lra

@@ -1,0 +1,88 @@
+// Launch wrappers of the CUDA kernels (one translation unit per family).
+// All matrices follow the library's internal layouts:
+//   X            : storage dtype, column-major, leading dimension ldx = dpad
+//                  (rows d..dpad-1 are zero), n columns.
+//   d x p blocks : FP32 column-major, leading dimension dpad, rows >= d zero.
+//   packed (rm)  : FP32 row-major with PP = pad_p(p) columns, zero padded.
+#pragma once
+
+#include "common.cuh"
+
+namespace lra {
+
+// ---- setup (k_setup.cu) ---------------------------------------------------
+void colnorms(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t d, int64_t n,
+              double *norm2);
+// out[0] = sum_i v_i (fixed-order), out[1] = max_i v_i; scratch >= 2 * 1024 doubles
+void sum_max(cudaStream_t s, const double *v, int64_t n, double *out, double *scratch);
+// Integer weights, their inclusive prefix sums (cum), c_i = total / w_i and
+// kappa = max_i (total / w_i) norm2_i.  scratch: >= ceil(n/1024) + 2048 uint64.
+void sampling_table(cudaStream_t s, const double *norm2, int64_t n, int mode, const double *maxn,
+                    uint64_t *cum, float *c, double *kappa_out, uint64_t *scratch);
+// idx[t] = first i with cum[i] > mulhi(u_t, total); cval[t] = c[idx[t]] if cval
+void sample(cudaStream_t s, const uint64_t *cum, int64_t n, uint64_t key, int64_t m, int32_t *idx,
+            const float *c, float *cval);
+// cval[t] = c[idx[t]]; bad[0] = 1 if an index is outside [0, n)
+void gather_c(cudaStream_t s, const int32_t *idx, const float *c, int64_t m, int64_t n, float *cval,
+              int *bad);
+// Box-Muller N(0,1) block (dpad x p, rows >= d left zero)
+void gaussian(cudaStream_t s, uint64_t key, int64_t d, int64_t dpad, int p, float *out);
+// storage conversions (column-major, any ld -> dpad)
+void convert_to_f32(cudaStream_t s, const void *src, lra_dtype sdt, int64_t ld, int64_t d,
+                    int64_t ncols, float *dst, int64_t dpad);
+void convert_to_bf16(cudaStream_t s, const void *src, lra_dtype sdt, int64_t ld, int64_t d,
+                     int64_t ncols, __nv_bfloat16 *dst, int64_t dpad);
+
+// ---- anchor pass (k_anchor.cu) --------------------------------------------
+// Wr (dpad x PP row-major) <- W (dpad x p column-major, leading dim ldw)
+void pack_rm(cudaStream_t s, const float *W, int64_t ldw, int64_t rows, int p, int PP, float *Wr);
+// Y (n x PP row-major) = X^T Wr
+void xtw(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int64_t n,
+         const float *Wr, int PP, float *Y);
+// partial G over column chunks: Gp[c] (dpad x PP row-major) = X[:, chunk c] Y[chunk c, :]
+int xy_chunks(int64_t dpad, int64_t n);
+void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int64_t n,
+        const float *Y, int PP, float *Gp, int nchunks);
+// M = lambda Wt - sum_c Gp[c] - B (dpad x p column-major); if norms: norms[0] =
+// ||M||_F^2, norms[1] = ||B||_F^2 (FP64).  If M == nullptr: G = sum_c Gp[c] is
+// written to G (dpad x p) instead.  scratch >= 2 * (dpad/32) doubles.
+void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
+                     double lam, const float *Wt, const float *B, float *M, double *norms,
+                     double *scratch);
+
+// ---- SVRG inner loop (k_inner.cu) -----------------------------------------
+void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
+                float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
+                int64_t m, float eta, float lam);
+
+// ---- p x p and d x p helpers (k_small.cu) -------------------------------
+// G (p x p FP64, column-major) = A^T A, A rows x p with strides (rs, cs).
+// scratch >= gram_scratch(p) doubles
+int64_t gram_scratch(int p);
+void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, int p, double *G,
+          double *scratch);
+// Cholesky G = R^T R (upper R), Rinv = R^-1 as FP32 p x p row-major;
+// status[0] = 0 ok / 1 not positive definite
+void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status);
+// Out (rows x q) = A (rows x p) T (p x q, FP32 row-major); strides for A and Out
+void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int64_t acs, int p,
+                 const float *T, int q, float *Out, int64_t ors, int64_t ocs);
+// Symmetric eigendecomposition of H (p x p FP64 column-major); evals desc,
+// evecs column-major FP64 (largest |entry| positive).  work >= sym_eig_work(p) doubles.
+int64_t sym_eig_work(int p);
+void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work);
+// P (p x p FP32 row-major) = V_k diag(f(rho)) V_k^T with f = 1/(lam - rho):
+// the Galerkin inverse (lam I - H)^-1 on the Ritz basis.  kcols = p.
+void ritz_inverse(cudaStream_t s, const double *evecs, const double *evals, int p, double lam,
+                  float *P);
+// T (p x k FP32 row-major) = first k columns of evecs
+void evecs_to_rm(cudaStream_t s, const double *evecs, int p, int k, float *T);
+// out[j] = sum_r A[r, j] B[r, j] (FP64) for j < p (column-major, leading dim ld)
+void col_dots(cudaStream_t s, const float *A, const float *B, int64_t rows, int64_t ld, int p,
+              double *out);
+// A[:, j] *= 1/sqrt(n2[j])  (n2 device FP64)
+void scale_cols_rsqrt(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, const double *n2);
+// A = alpha * A (all rows x p)
+void scale_block(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, float alpha);
+
+}  // namespace lra
