@@ -220,6 +220,25 @@ lra_status lra_colnorms(lra_mat *mat, double *norm2, double *fro2);
 lra_status lra_sampling_table(lra_ctx *ctx, int64_t n, const double *norm2, int mode,
                               uint64_t *cum, float *c, uint64_t *total, double *kappa);
 
+/* Largest n accepted by lra_sampling_table_noalloc. */
+#define LRA_NOALLOC_MAX_N (1ll << 24)
+
+/* The same table as lra_sampling_table, built without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc / cudaFree when they build the table (for instance an
+ * application whose framework reserves the GPU memory for its own pool, or one
+ * that cannot afford the device-wide synchronisation of cudaFree mid-stream).
+ * Inputs and outputs are the caller's, as for lra_sampling_table; the scratch
+ * (about 0.5 MB) is a fixed device array of the library that stays resident on
+ * every GPU that loads the library, until exit.  Requires 1 <= n <=
+ * LRA_NOALLOC_MAX_N (LRA_EINVAL otherwise).  Calls no cudaMalloc, cudaFree or
+ * allocating library routine.  All calls share the array: calls whose GPU work
+ * overlaps (other streams or threads) race on it and must be serialised by the
+ * caller.  The first call on a device looks the array's address up with that
+ * device current; make it before any stream capture. */
+lra_status lra_sampling_table_noalloc(lra_ctx *ctx, int64_t n, const double *norm2, int mode,
+                                      uint64_t *cum, float *c, uint64_t *total, double *kappa);
+
 /* Sampler (a7): idx[t] (device, m int32) = the first i with cum[i] > r_t,
  * r_t = floor(u_t * total / 2^64), u_t the t-th word of stream `key`. */
 lra_status lra_sample(lra_ctx *ctx, int64_t n, const uint64_t *cum, uint64_t total, uint64_t key,

@@ -10,7 +10,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
-from ._ffi import (LRA_BF16, LRA_F16, LRA_F32, LRA_F64, LRA_MAX_P, LRA_SAMPLE_IMPORTANCE,
+from ._ffi import (LRA_BF16, LRA_F16, LRA_F32, LRA_F64, LRA_MAX_P, LRA_NOALLOC_MAX_N,
+                   LRA_SAMPLE_IMPORTANCE,
                    LRA_SAMPLE_UNIFORM, LRA_SHIFT_FAR, LRA_SHIFT_FIXED, LRA_SHIFT_PAPER,
                    LRA_STREAM_DELTA, LRA_STREAM_INIT, LRA_STREAM_POWER_A, LRA_STREAM_POWER_D,
                    LRA_STREAM_SVRG, STATUS, LraError, LraOptions, LraReport, LraSolveInfo,
@@ -129,6 +130,13 @@ def lra_sampling_table(ctx, n, norm2, mode, cum, c):
     tot, kap = C.c_uint64(), C.c_double()
     _check(lib.lra_sampling_table(ctx, n, _p(norm2), mode, _p(cum), _p(c), C.byref(tot),
                                   C.byref(kap)))
+    return tot.value, kap.value
+
+
+def lra_sampling_table_noalloc(ctx, n, norm2, mode, cum, c):
+    tot, kap = C.c_uint64(), C.c_double()
+    _check(lib.lra_sampling_table_noalloc(ctx, n, _p(norm2), mode, _p(cum), _p(c), C.byref(tot),
+                                          C.byref(kap)))
     return tot.value, kap.value
 
 

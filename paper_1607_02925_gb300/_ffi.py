@@ -19,6 +19,7 @@ LRA_SHIFT_PAPER, LRA_SHIFT_FAR, LRA_SHIFT_FIXED = 0, 1, 2
 LRA_SAMPLE_IMPORTANCE, LRA_SAMPLE_UNIFORM = 0, 1
 LRA_STREAM_INIT, LRA_STREAM_POWER_A, LRA_STREAM_POWER_D, LRA_STREAM_SVRG, LRA_STREAM_DELTA = 1, 2, 3, 4, 5
 LRA_MAX_P = 112
+LRA_NOALLOC_MAX_N = 1 << 24
 STATUS = ["LRA_OK", "LRA_EINVAL", "LRA_ENOMEM", "LRA_ECUDA", "LRA_ENOTCONV", "LRA_EDIVERGED",
           "LRA_ENUMERIC", "LRA_ETIMEOUT", "LRA_EAGAIN", "LRA_EBUSY", "LRA_ECANCELLED",
           "LRA_EUNSUPPORTED"]
@@ -128,6 +129,7 @@ _PROTOS = {
     "lra_stream_key": (u64, [u64, u64, u64, u64]),
     "lra_colnorms": (ci, [vp, vp, vp]),
     "lra_sampling_table": (ci, [vp, i64, vp, ci, vp, vp, vp, vp]),
+    "lra_sampling_table_noalloc": (ci, [vp, i64, vp, ci, vp, vp, vp, vp]),
     "lra_sample": (ci, [vp, i64, vp, u64, u64, i64, vp]),
     "lra_gaussian_block": (ci, [vp, u64, u64, u64, i64, ci, vp]),
     "lra_anchor": (ci, [vp, ci, vp, vp, dbl, vp, vp, vp]),

@@ -1,0 +1,107 @@
+// lra_sampling_table_noalloc: the sampling-distribution builder of
+// lra_sampling_table with its scratch memory in a fixed device array of this
+// library instead of memory allocated per call.
+//
+// Who needs it: a caller that cannot call cudaMalloc/cudaFree at the point it
+// builds the table, e.g. an application whose framework has reserved the GPU's
+// memory for its own pool allocator, or one that must not take the device-wide
+// synchronisation that cudaFree implies in the middle of its own stream work.
+// The caller still provides the inputs and outputs.
+//
+// The scratch array lives for as long as the library is loaded, on every GPU
+// that loads it.  All calls share it: two calls whose work overlaps on the GPU
+// (different streams or threads) race on it and must be serialised by the
+// caller.  The first call on a device looks up the array's device address with
+// that device current; make that first call before any stream capture.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "engine.h"
+
+namespace lra {
+namespace {
+
+// Tile sums of the scan (ceil(n/1024) uint64) and per-block maxima of the
+// c-vector kernel (ceil(n/256) doubles, reusing the same words), plus 4
+// doubles for sum, max and kappa.
+constexpr int64_t kScratchWords = LRA_NOALLOC_MAX_N / 256 + 64;
+__device__ __align__(256) uint64_t g_table_scratch[kScratchWords];
+
+std::mutex g_addr_mu;
+void *g_addr[64] = {nullptr};
+
+// Device address of g_table_scratch on the current device (looked up once).
+uint64_t *scratch_address(int device) {
+    std::lock_guard<std::mutex> g(g_addr_mu);
+    if (device < 0 || device >= 64) {
+        set_error("device index out of range for the fixed scratch table");
+        throw Error{LRA_EUNSUPPORTED};
+    }
+    if (!g_addr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_table_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            throw Error{LRA_ECUDA};
+        }
+        g_addr[device] = ptr;
+    }
+    return static_cast<uint64_t *>(g_addr[device]);
+}
+
+}  // namespace
+}  // namespace lra
+
+extern "C" lra_status lra_sampling_table_noalloc(lra_ctx *ctx, int64_t n, const double *norm2, int mode,
+                                                 uint64_t *cum, float *c, uint64_t *total,
+                                                 double *kappa) {
+    using namespace lra;
+    if (!ctx || !norm2 || !cum || !c || n < 1) {
+        set_error("null argument or n < 1");
+        return LRA_EINVAL;
+    }
+    if (n > LRA_NOALLOC_MAX_N) {
+        set_error("n exceeds LRA_NOALLOC_MAX_N, the size of the fixed scratch array");
+        return LRA_EINVAL;
+    }
+    if (mode != LRA_SAMPLE_IMPORTANCE && mode != LRA_SAMPLE_UNIFORM) {
+        set_error("bad mode");
+        return LRA_EINVAL;
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    try {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != ctx->device) LRA_CUDA(cudaSetDevice(ctx->device));
+        struct Restore {
+            int d;
+            ~Restore() {
+                if (d >= 0) cudaSetDevice(d);
+            }
+        } restore{prev != ctx->device ? prev : -1};
+        uint64_t *scr = scratch_address(ctx->device);
+        const cudaStream_t s = ctx->stream;
+        const int64_t words = ceil_div(n, 256) + 16;
+        double *sm = reinterpret_cast<double *>(scr + kScratchWords - 8);  // sum, max, kappa
+        // the array keeps the previous call's contents: clear what this call uses
+        LRA_CUDA(cudaMemsetAsync(scr, 0, sizeof(uint64_t) * words, s));
+        LRA_CUDA(cudaMemsetAsync(sm, 0, sizeof(double) * 4, s));
+        sum_max(s, norm2, n, sm, nullptr);
+        sampling_table(s, norm2, n, mode, sm + 1, cum, c, sm + 2, scr);
+        uint64_t tot = 0;
+        double kp = 0.0;
+        LRA_CUDA(cudaMemcpyAsync(&tot, cum + n - 1, sizeof(tot), cudaMemcpyDeviceToHost, s));
+        LRA_CUDA(cudaMemcpyAsync(&kp, sm + 2, sizeof(kp), cudaMemcpyDeviceToHost, s));
+        LRA_CUDA(cudaStreamSynchronize(s));
+        if (total) *total = tot;
+        if (kappa) *kappa = kp;
+        return LRA_OK;
+    } catch (const Error &e) {
+        return e.st;
+    } catch (...) {
+        set_error("unexpected exception");
+        return LRA_ECUDA;
+    }
+}
