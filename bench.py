@@ -288,14 +288,19 @@ def run_lra(args):
         flops_l = 2.0 * wl.d * wl.n * pav
         t_l = tot[dom] / cnt[dom] / 1e3
         hbm = peaks["hbm_gbs"] * 1e9
-        alu = 152 * 128 * 2 * sm_mhz * 1e6   # FP32 FMA lanes x 2 flop x clock
+        # both storages run the X passes on tensor cores: BF16 X with 2 BF16 MMAs
+        # per k-step (hi/lo small operand), FP32 X as a BF16 pair with 3; the
+        # executed tensor flops are compared with the measured sustained BF16 peak
+        tensor = True
+        mmas = 2 if args.storage == "bf16" else 3
+        alu = peaks["bf16_tflops_sustained"] * 1e12 / mmas
         if bytes_l / hbm >= flops_l / alu:
             roof = {"bound": "hbm", "achieved": bytes_l / t_l / 1e9, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": bytes_l / t_l / hbm, "traffic": None}
         else:
-            roof = {"bound": "alu", "achieved": flops_l / t_l / 1e12, "peak": alu / 1e12,
+            roof = {"bound": "tensor" if tensor else "alu", "achieved": flops_l / t_l / 1e12, "peak": alu / 1e12,
                     "unit": "TFLOP/s", "frac": flops_l / t_l / alu, "traffic": None}
-        roof.update({"kernel": "xtw_kernel" if dom == "xtw" else "xy_kernel",
+        roof.update({"kernel": ("xtw" if dom == "xtw" else "xy") + ("_tc_kernel" if tensor else "_kernel"),
                      "launches": cnt[dom], "ms_per_launch": t_l * 1e3,
                      "algorithmic_bytes_per_launch": bytes_l,
                      "x_pass_gbs": bytes_l / t_l / 1e9, "peak_source": peak_kind})

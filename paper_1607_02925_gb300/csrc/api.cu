@@ -239,8 +239,16 @@ lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, c
                 }
                 if (!dev) LRA_CUDA(cudaStreamSynchronize(s));
             }
+            if (storage == LRA_F32) {
+                // the tensor-core passes stream the FP32 values as a BF16 pair
+                m->Xh = static_cast<__nv_bfloat16 *>(dev_alloc(ctx, sizeof(__nv_bfloat16) * ncell));
+                m->Xl = static_cast<__nv_bfloat16 *>(dev_alloc(ctx, sizeof(__nv_bfloat16) * ncell));
+                split_hilo(s, m->X32, (int64_t)ncell, m->Xh, m->Xl);
+            }
             LRA_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
+            if (m->Xh) dev_free(ctx, m->Xh, sizeof(__nv_bfloat16) * ncell);
+            if (m->Xl) dev_free(ctx, m->Xl, sizeof(__nv_bfloat16) * ncell);
             cudaStreamSynchronize(ctx->stream);
             if (stage) dev_free(ctx, stage, stage_bytes);
             if (m->X && m->X != m->X32) dev_free(ctx, m->X, sizeof(__nv_bfloat16) * ncell);
@@ -278,6 +286,8 @@ lra_status lra_mat_destroy(lra_mat *m) {
         const size_t ncell = (size_t)m->dpad * m->n;
         if (m->X && m->X != m->X32) dev_free(ctx, m->X, sizeof(__nv_bfloat16) * ncell);
         if (m->X32) dev_free(ctx, m->X32, sizeof(float) * ncell);
+        if (m->Xh) dev_free(ctx, m->Xh, sizeof(__nv_bfloat16) * ncell);
+        if (m->Xl) dev_free(ctx, m->Xl, sizeof(__nv_bfloat16) * ncell);
         if (m->norm2) dev_free(ctx, m->norm2, sizeof(double) * m->n);
         if (m->dev_sm) dev_free(ctx, m->dev_sm, sizeof(double) * 4);
         for (auto &t : m->table) {

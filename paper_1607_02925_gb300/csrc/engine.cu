@@ -120,6 +120,11 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
         Rinv = alloc<float>(pp);
         P = alloc<float>(pp);
         status = alloc<int>(4);
+        tcerr = alloc<int>(4);
+        LRA_CUDA(cudaMemset(tcerr, 0, sizeof(int) * 4));
+        ldy = tc_ldy(n);
+        Wb = alloc<__nv_bfloat16>((size_t)2 * PPmax * dpad);
+        Yb = alloc<__nv_bfloat16>((size_t)2 * PPmax * ldy);
         LRA_CUDA(cudaMallocHost(&host, sizeof(double) * (2 * pmax + 16)));
     } catch (...) {
         for (auto &a : allocs) dev_free(ctx, a.first, a.second);
@@ -251,45 +256,83 @@ const lra_mat::Table &Engine::ensure_table(int mode) {
     return t;
 }
 
+void Engine::check_tc() {
+    int e = 0;
+    LRA_CUDA(cudaMemcpyAsync(&e, ws_.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    sync();
+    if (e) {
+        set_error("a tensor-core pipeline wait timed out");
+        throw Error{LRA_ETIMEOUT};
+    }
+}
+
 void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
     const int PP = pad_p(p);
-    pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
-    if (timer) timer->begin(KernelTimer::XTW, p);
-    xtw(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, ws_.Wr, PP, Y);
-    if (timer) timer->end();
+    if (tc(use32)) {
+        pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
+        if (timer) timer->begin(KernelTimer::XTW, p);
+        xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, ws_.Yb,
+               ws_.ldy, ws_.tcerr);
+        if (timer) timer->end();
+    } else {
+        pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
+        if (timer) timer->begin(KernelTimer::XTW, p);
+        xtw(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, ws_.Wr, PP, Y);
+        if (timer) timer->end();
+    }
+    stats.x_passes += 1;
+}
+
+void Engine::xy_pass(const float *Y32, int p, bool use32) {
+    const int PP = pad_p(p);
+    if (tc(use32)) {
+        if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
+        if (timer) timer->begin(KernelTimer::XY, p);
+        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp,
+              ws_.nchunks, ws_.tcerr);
+        if (timer) timer->end();
+    } else {
+        if (timer) timer->begin(KernelTimer::XY, p);
+        xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y32, PP, ws_.Gp, ws_.nchunks);
+        if (timer) timer->end();
+    }
     stats.x_passes += 1;
 }
 
 void Engine::x_mul(const float *Y, int p, float *G, bool use32) {
-    const int PP = pad_p(p);
-    if (timer) timer->begin(KernelTimer::XY, p);
-    xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y, PP, ws_.Gp, ws_.nchunks);
-    if (timer) timer->end();
-    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, PP, p, 0.0, nullptr, nullptr, G, nullptr,
+    xy_pass(Y, p, use32);
+    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
                     ws_.epi);
-    stats.x_passes += 1;
 }
 
 void Engine::a_apply(const float *W, int p, float *G) {
-    xt_mul(W, p, ws_.Y, false);
-    x_mul(ws_.Y, p, G, false);
+    if (tc(false)) {
+        xt_mul(W, p, nullptr, false);
+        xy_pass(nullptr, p, false);
+    } else {
+        xt_mul(W, p, ws_.Y, false);
+        xy_pass(ws_.Y, p, false);
+    }
+    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
+                    ws_.epi);
 }
 
 void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *Y0,
                     double *nM2, double *nB2) {
     const int PP = pad_p(p);
-    const float *Y = Y0;
-    if (!Y) {
+    if (Y0) {
+        xy_pass(Y0, p, false);
+    } else if (tc(false)) {
+        xt_mul(Wt, p, nullptr, false);
+        xy_pass(nullptr, p, false);
+    } else {
         xt_mul(Wt, p, ws_.Y, false);
-        Y = ws_.Y;
+        xy_pass(ws_.Y, p, false);
     }
-    if (timer) timer->begin(KernelTimer::XY, p);
-    xy(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, mat_->n, Y, PP, ws_.Gp, ws_.nchunks);
-    if (timer) timer->end();
-    stats.x_passes += 1;
     anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
     if (nM2 || nB2) {
         LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        if (tc(false)) check_tc();
         sync();
         if (nM2) *nM2 = ws_.host[0];
         if (nB2) *nB2 = ws_.host[1];
@@ -612,10 +655,12 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     R.ms_outer = ms_since(t0);
 
     t0 = std::chrono::steady_clock::now();
-    if (mat_->storage == LRA_BF16) {
-        // Algorithm 2 on the FP32 values of X: the answer is measured there
+    if (tc(false)) {
+        // Algorithm 2 on the exact FP32 values of X (the iteration streamed X as
+        // BF16 or as a BF16 pair): the answer is measured there
         ritz(S, p, true);
     }
+    if (tc(false)) check_tc();
     evecs_to_rm(s_, ws_.evecs, p, k, ws_.P);
     apply_right(s_, S, dpad, 1, dpad, p, ws_.P, k, ws_.U, 1, dpad);
     LRA_CUDA(cudaMemcpy2DAsync(U, sizeof(float) * d, ws_.U, sizeof(float) * dpad, sizeof(float) * d, k,

@@ -33,6 +33,9 @@ struct lra_mat {
     lra_dtype storage = LRA_F32;
     void *X = nullptr;     // storage dtype, dpad x n column-major
     float *X32 = nullptr;  // FP32 copy (== X when storage is FP32)
+    // FP32 storage: BF16 pair (x = hi + lo + r, |r| <= 2^-17 |x|) streamed by the
+    // tensor-core X passes; null for BF16 storage
+    __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
     // setup cache (a0)
     std::mutex setup_mu;
     bool have_norms = false;
@@ -117,7 +120,10 @@ struct Workspace {
     double *H = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;
+    __nv_bfloat16 *Wb = nullptr, *Yb = nullptr;  // BF16 hi/lo operands of the tensor-core passes
+    int64_t ldy = 0;
     int *status = nullptr;
+    int *tcerr = nullptr;  // error word of the tensor-core kernels
     int32_t *idx = nullptr;
     float *cval = nullptr;
     int64_t idx_cap = 0;
@@ -175,10 +181,19 @@ class Engine {
                      double *ritz, lra_report *rep, const std::atomic<int> *cancel);
 
     void sync();
+    void check_tc();  // raise if a tensor-core kernel reported a timed-out wait
     Stats stats;
     KernelTimer *timer = nullptr;
 
    private:
+    // tensor-core passes: BF16 X, or the BF16 pair of an FP32 X; the exact FP32
+    // values (use32) go through the CUDA-core kernels
+    bool tc(bool use32) const { return !use32 && (mat_->storage == LRA_BF16 || mat_->Xh != nullptr); }
+    const __nv_bfloat16 *tcx() const {
+        return mat_->Xh ? mat_->Xh : static_cast<const __nv_bfloat16 *>(mat_->X);
+    }
+    // G-partials of one X Y pass into ws.Gp; Y32 == nullptr means ws.Yb already holds Y
+    void xy_pass(const float *Y32, int p, bool use32);
     const void *xptr(bool use32) const { return use32 ? (const void *)mat_->X32 : mat_->X; }
     lra_dtype xdt(bool use32) const { return use32 ? LRA_F32 : mat_->storage; }
     lra_mat *mat_;

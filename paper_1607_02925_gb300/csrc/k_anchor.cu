@@ -298,10 +298,10 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int ts = PP + 1;
     for (int e = tid; e < 32 * PP; e += 256) {
-        double acc = 0.0;
+        float acc = 0.0f;  // a few dozen chunk partials: FP32, fixed order
         const int64_t off = r0 * PP + e;
-        for (int c = 0; c < nchunks; ++c) acc += (double)Gp[(int64_t)c * dpad * PP + off];
-        tile[(e / PP) * ts + (e % PP)] = (float)acc;
+        for (int c = 0; c < nchunks; ++c) acc += Gp[(int64_t)c * dpad * PP + off];
+        tile[(e / PP) * ts + (e % PP)] = acc;
     }
     __syncthreads();
     double m2 = 0.0, b2 = 0.0;
@@ -339,13 +339,16 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__
     }
 }
 
+// one warp: strided partial sums, then a fixed shuffle tree (deterministic)
 __global__ void norms_final_kernel(const double *__restrict__ partial, int nb, double *__restrict__ norms) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) {
+        a0 += partial[2 * b];
+        a1 += partial[2 * b + 1];
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
     if (threadIdx.x == 0) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            a0 += partial[2 * b];
-            a1 += partial[2 * b + 1];
-        }
         norms[0] = a0;
         norms[1] = a1;
     }

@@ -1,0 +1,436 @@
+// Anchor-pass products on the 5th-generation tensor cores (tcgen05), for X
+// stored in BF16:
+//   xtw_tc_kernel: Y = X^T W  — M = 128 data points per CTA, N = PP, K = d.
+//   xy_tc_kernel:  G = X Y    — M = 128 rows of X per CTA, N = PP, K = a chunk
+//                               of columns (split-K; fixed-order reduction after).
+// X tiles and the small operand stream through shared memory by TMA
+// (128-byte swizzle) in a multi-stage mbarrier pipeline; one thread issues the
+// MMAs into a TMEM accumulator; four warps read it back with tcgen05.ld.  The
+// FP32 small operand is split into BF16 hi + lo, both multiplied into the same
+// accumulator, so its rounding error is ~2^-17 instead of 2^-9.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace lra {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128;                // rows of the MMA tile
+constexpr int kBK = 64;                 // K elements per pipeline stage (128 B of BF16)
+constexpr int kATile = kBM * kBK * 2;   // 16 KB
+constexpr int kTmemCols = 128;          // accumulator columns allocated (PP <= 112)
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// NA = 1: X stored in BF16.  NA = 2: X stored in FP32 and streamed as its
+// BF16 hi + lo pair (x = hi + lo + r, |r| <= 2^-17 |x|).
+template <int PP, int NA>
+struct Tile {
+    static constexpr int kA = NA * kATile;
+    static constexpr int kB = PP * 128;             // one of hi / lo: PP rows x 128 B
+    static constexpr int kStage = kA + 2 * kB;      // multiple of 1024
+    static constexpr int kStages = NA == 1 ? (PP <= 64 ? 3 : 4) : (kStage <= 50 * 1024 ? 4 : 3);
+    static constexpr int kSmem = kStages * kStage + 1024 + 256;
+};
+
+// Shared tail of both kernels: barriers and the TMEM address slot after the stages.
+struct Ctl {
+    uint64_t full[4], empty[4], accum;
+    uint32_t tmem;
+};
+
+// ---------------------------------------------------------------------------
+// Y = X^T W
+// ---------------------------------------------------------------------------
+template <int PP, int NA>
+__global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                        const __grid_constant__ CUtensorMap tmXl,
+                                                        const __grid_constant__ CUtensorMap tmW,
+                                                        int nkb, int64_t n, float *__restrict__ Y32,
+                                                        __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
+                                                        int *__restrict__ err) {
+    using T = Tile<PP, NA>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = (int64_t)blockIdx.x * kBM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < T::kStages; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        mbar_init(&ctl->accum, 1);
+        fence_barrier_init();
+        prefetch_tmap(&tmX);
+        if (NA == 2) prefetch_tmap(&tmXl);
+        prefetch_tmap(&tmW);
+    }
+    if (warp == 0) {
+        tmem_alloc(&ctl->tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % T::kStages;
+            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            uint8_t *a = smem + st * T::kStage;
+            mbar_expect_tx(&ctl->full[st], T::kStage);
+            tma_load_2d(a, &tmX, kb * kBK, (int)i0, &ctl->full[st]);
+            if (NA == 2) tma_load_2d(a + kATile, &tmXl, kb * kBK, (int)i0, &ctl->full[st]);
+            tma_load_2d(a + T::kA, &tmW, kb * kBK, 0, &ctl->full[st]);
+            tma_load_2d(a + T::kA + T::kB, &tmW, kb * kBK, PP, &ctl->full[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(1, 0, 0, PP, kBM);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % T::kStages;
+            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
+            if (!mbar_wait(&ctl->full[st], ph)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + st * T::kStage);
+            const uint32_t bh = a + T::kA, bl = bh + T::kB;
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint64_t ad = sw128_desc(a + ks * 32, 16, 1024);
+                const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                mma_f16(tmem, ad, bhd, idesc, (kb | ks) != 0);
+                mma_f16(tmem, ad, sw128_desc(bl + ks * 32, 16, 1024), idesc, 1u);
+                if (NA == 2) mma_f16(tmem, sw128_desc(a + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+            }
+            mma_commit(&ctl->empty[st]);
+        }
+        mma_commit(&ctl->accum);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows i0 + 32w + lane)
+    const bool ok = mbar_wait(&ctl->accum, 0);
+    tc_fence_after();
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+    } else {
+        const int64_t i = i0 + warp * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < PP; c += 16) {
+            float v[16];
+            tmem_ld16(tl + c, v);
+            if (i < n) {
+                if (Y32) {
+                    float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (Yb) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                        Yb[(int64_t)(c + j) * ldy + i] = hi;
+                        Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Partial G = X[rows, chunk] Y[chunk, :]  (X is the MN-major operand here)
+// ---------------------------------------------------------------------------
+template <int PP, int NA>
+__global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                       const __grid_constant__ CUtensorMap tmXl,
+                                                       const __grid_constant__ CUtensorMap tmY,
+                                                       int64_t cols_per_chunk, int64_t n, int64_t dpad,
+                                                       float *__restrict__ Gp, int *__restrict__ err) {
+    using T = Tile<PP, NA>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * kBM;
+    const int64_t c0 = (int64_t)blockIdx.y * cols_per_chunk;
+    const int64_t c1 = (c0 + cols_per_chunk < n) ? c0 + cols_per_chunk : n;
+    const int nkb = c1 > c0 ? (int)((c1 - c0 + kBK - 1) / kBK) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < T::kStages; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        mbar_init(&ctl->accum, 1);
+        fence_barrier_init();
+        prefetch_tmap(&tmX);
+        if (NA == 2) prefetch_tmap(&tmXl);
+        prefetch_tmap(&tmY);
+    }
+    if (warp == 0) {
+        tmem_alloc(&ctl->tmem, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % T::kStages;
+            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            uint8_t *a = smem + st * T::kStage;
+            const int col = (int)(c0 + (int64_t)kb * kBK);
+            mbar_expect_tx(&ctl->full[st], T::kStage);
+            tma_load_2d(a, &tmX, (int)r0, col, &ctl->full[st]);
+            tma_load_2d(a + kATile / 2, &tmX, (int)r0 + 64, col, &ctl->full[st]);
+            if (NA == 2) {
+                tma_load_2d(a + kATile, &tmXl, (int)r0, col, &ctl->full[st]);
+                tma_load_2d(a + kATile + kATile / 2, &tmXl, (int)r0 + 64, col, &ctl->full[st]);
+            }
+            tma_load_2d(a + T::kA, &tmY, col, 0, &ctl->full[st]);
+            tma_load_2d(a + T::kA + T::kB, &tmY, col, PP, &ctl->full[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = instr_desc(1, 1, 0, PP, kBM);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % T::kStages;
+            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
+            if (!mbar_wait(&ctl->full[st], ph)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a = smem_u32(smem + st * T::kStage);
+            const uint32_t bh = a + T::kA, bl = bh + T::kB;
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+                // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
+                const uint64_t ad = sw128_desc(a + ks * 2048, kATile / 2, 1024);
+                const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                mma_f16(tmem, ad, bhd, idesc, (kb | ks) != 0);
+                mma_f16(tmem, ad, sw128_desc(bl + ks * 32, 16, 1024), idesc, 1u);
+                if (NA == 2) mma_f16(tmem, sw128_desc(a + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+            }
+            mma_commit(&ctl->empty[st]);
+        }
+        mma_commit(&ctl->accum);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(&ctl->accum, 0);
+    tc_fence_after();
+    const int64_t r = r0 + warp * 32 + lane;
+    float *out = Gp + (int64_t)blockIdx.y * dpad * PP + r * PP;
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+    } else {
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c = 0; c < PP; c += 16) {
+            float v[16];
+            if (nkb > 0) {
+                tmem_ld16(tl + c, v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(out + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation
+// ---------------------------------------------------------------------------
+// Wb[j][r] = hi / Wb[PP + j][r] = lo of W[r + j ld] (zero for j >= p)
+__global__ void pack_hilo_kernel(const float *__restrict__ W, int64_t ld, int64_t rows, int p, int PP,
+                                 __nv_bfloat16 *__restrict__ Wb) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * PP) return;
+    const int j = (int)(e / rows);
+    const int64_t r = e % rows;
+    const float w = j < p ? W[r + (int64_t)j * ld] : 0.0f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+    Wb[e] = hi;
+    Wb[(int64_t)PP * rows + e] = __float2bfloat16_rn(w - __bfloat162float(hi));
+}
+
+// X (FP32, dpad x ncols) -> BF16 hi + lo with x = hi + lo + r, |r| <= 2^-17 |x|
+__global__ void split_hilo_kernel(const float *__restrict__ X, int64_t count, __nv_bfloat16 *__restrict__ Xh,
+                                  __nv_bfloat16 *__restrict__ Xl) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float x = X[e];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        Xh[e] = hi;
+        Xl[e] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+// Yb (hi/lo, column-major, leading dim ldy) from Y (n x PP row-major FP32)
+__global__ void y_hilo_kernel(const float *__restrict__ Y, int64_t n, int PP, __nv_bfloat16 *__restrict__ Yb,
+                              int64_t ldy) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * PP) return;
+    const int j = (int)(e / n);
+    const int64_t i = e % n;
+    const float y = Y[i * PP + j];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+    Yb[(int64_t)j * ldy + i] = hi;
+    Yb[(int64_t)(PP + j) * ldy + i] = __float2bfloat16_rn(y - __bfloat162float(hi));
+}
+
+// ---------------------------------------------------------------------------
+// host: tensor maps
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        LRA_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) {
+            set_error("cuTensorMapEncodeTiled not available");
+            throw Error{LRA_ECUDA};
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor: dim0 (contiguous) = e0 elements, dim1 = e1, row pitch ld0
+// elements; box = b0 x b1; 128-byte swizzle; out-of-range reads return 0.
+CUtensorMap make_map(const void *base, uint64_t e0, uint64_t e1, uint64_t ld0, uint32_t b0, uint32_t b1) {
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {e0, e1};
+    const cuuint64_t strides[1] = {ld0 * 2};
+    const cuuint32_t box[2] = {b0, b1};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        throw Error{LRA_ECUDA};
+    }
+    return m;
+}
+
+template <typename F>
+void dispatch_tc_pp(int PP, F &&f) {
+    switch (PP) {
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        case 32: f(std::integral_constant<int, 32>{}); break;
+        case 48: f(std::integral_constant<int, 48>{}); break;
+        case 64: f(std::integral_constant<int, 64>{}); break;
+        case 80: f(std::integral_constant<int, 80>{}); break;
+        case 96: f(std::integral_constant<int, 96>{}); break;
+        case 112: f(std::integral_constant<int, 112>{}); break;
+        default:
+            set_error("unsupported padded p " + std::to_string(PP));
+            throw Error{LRA_EUNSUPPORTED};
+    }
+}
+
+}  // namespace
+
+int64_t tc_ldy(int64_t n) { return round_up(n, 64); }
+
+void pack_hilo(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, __nv_bfloat16 *Wb) {
+    pack_hilo_kernel<<<(unsigned)ceil_div(rows * PP, 256), 256, 0, s>>>(W, ld, rows, p, PP, Wb);
+    LRA_LAUNCHED();
+}
+
+void y_hilo(cudaStream_t s, const float *Y, int64_t n, int PP, __nv_bfloat16 *Yb, int64_t ldy) {
+    y_hilo_kernel<<<(unsigned)ceil_div(n * PP, 256), 256, 0, s>>>(Y, n, PP, Yb, ldy);
+    LRA_LAUNCHED();
+}
+
+void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 64);
+    split_hilo_kernel<<<blocks, 256, 0, s>>>(X, count, Xh, Xl);
+    LRA_LAUNCHED();
+}
+
+void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
+            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err) {
+    const CUtensorMap mx = make_map(X, dpad, n, dpad, kBK, kBM);
+    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, kBK, kBM);
+    const CUtensorMap mw = make_map(Wb, dpad, 2 * PP, dpad, kBK, PP);
+    const int nkb = (int)(dpad / kBK);
+    dispatch_tc_pp(PP, [&](auto ppc) {
+        constexpr int P = decltype(ppc)::value;
+        auto launch = [&](auto kern, int smem) {
+            LRA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            kern<<<(unsigned)ceil_div(n, kBM), 128, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
+            LRA_LAUNCHED();
+        };
+        if (Xl)
+            launch(xtw_tc_kernel<P, 2>, Tile<P, 2>::kSmem);
+        else
+            launch(xtw_tc_kernel<P, 1>, Tile<P, 1>::kSmem);
+    });
+}
+
+void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
+           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err) {
+    const CUtensorMap mx = make_map(X, dpad, n, dpad, 64, kBK);
+    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, 64, kBK);
+    const CUtensorMap my = make_map(Yb, n, 2 * PP, ldy, kBK, PP);
+    const int64_t cpc = round_up(ceil_div(n, nchunks), kBK);
+    dispatch_tc_pp(PP, [&](auto ppc) {
+        constexpr int P = decltype(ppc)::value;
+        const dim3 grid((unsigned)(dpad / kBM), (unsigned)nchunks);
+        auto launch = [&](auto kern, int smem) {
+            LRA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            kern<<<grid, 128, smem, s>>>(mx, mxl, my, cpc, n, dpad, Gp, err);
+            LRA_LAUNCHED();
+        };
+        if (Xl)
+            launch(xy_tc_kernel<P, 2>, Tile<P, 2>::kSmem);
+        else
+            launch(xy_tc_kernel<P, 1>, Tile<P, 1>::kSmem);
+    });
+}
+
+}  // namespace lra

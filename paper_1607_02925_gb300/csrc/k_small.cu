@@ -236,9 +236,10 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ 
     int *pi = reinterpret_cast<int *>(sn + p2 / 2);  // [p2/2]
     int *pj = pi + p2 / 2;
     __shared__ double red_off[16], red_tot[16];
-    __shared__ int stop;
+    __shared__ int stop, rotated;
     const int tid = threadIdx.x, nt = blockDim.x;
     const T eps = sizeof(T) == 4 ? (T)1e-7 : (T)1e-15;
+    if (tid == 0) rotated = 0;
     for (int e = tid; e < p2 * p2; e += nt) {
         const int a = e / p2, b = e % p2;
         A[a * ld + b] = (a < p && b < p) ? (T)H[a + (int64_t)b * p] : (T)0;
@@ -268,8 +269,11 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ 
                 o += red_off[w];
                 t += red_tot[w];
             }
-            const double tol = sizeof(T) == 4 ? 1e-13 : 1e-28;  // squared relative
-            stop = (o <= tol * t) ? 1 : 0;
+            // squared relative off-diagonal mass: FP32 sweeps stop at 1e-5 (the
+            // FP64 refinement that follows squares it twice); FP64 at 1e-14
+            const double tol = sizeof(T) == 4 ? 1e-10 : 1e-28;
+            stop = (o <= tol * t || (sweep > 0 && !rotated)) ? 1 : 0;
+            rotated = 0;
         }
         __syncthreads();
         if (stop) break;
@@ -302,6 +306,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ 
                         t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
                     c = (T)1 / sqrt((T)1 + t * t);
                     s = t * c;
+                    rotated = 1;
                 }
                 cs[k] = c;
                 sn[k] = s;

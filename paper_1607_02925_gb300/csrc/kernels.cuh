@@ -50,6 +50,24 @@ void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
                      double *scratch);
 
+// ---- anchor pass on tensor cores, BF16 X (k_anchor_tc.cu) ---------------
+// leading dimension of the hi/lo BF16 copy of Y (n rounded up to 64)
+int64_t tc_ldy(int64_t n);
+// Wb = [hi; lo] BF16 split of W (rows x p column-major, leading dim ld), each
+// PP x rows column-major (zero for columns >= p)
+void pack_hilo(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, __nv_bfloat16 *Wb);
+// Yb = [hi; lo] BF16 split of Y (n x PP row-major), each PP x ldy column-major
+void y_hilo(cudaStream_t s, const float *Y, int64_t n, int PP, __nv_bfloat16 *Yb, int64_t ldy);
+// FP32 X -> BF16 pair (x = hi + lo + r, |r| <= 2^-17 |x|), count elements
+void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl);
+// Y = X^T W on tcgen05: writes Y32 (n x PP row-major) and/or Yb (hi/lo) when
+// non-null.  X is BF16 (Xl == nullptr) or the BF16 pair (X, Xl) of an FP32 X.
+void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
+            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err);
+// partial G = X Y per column chunk on tcgen05 (same Gp layout as xy)
+void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
+           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err);
+
 // ---- SVRG inner loop (k_inner.cu) -----------------------------------------
 void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
                 float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
