@@ -115,7 +115,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
         gscr = alloc<double>(gram_scratch(pmax));
         Gm = alloc<double>(pp);
         norms = alloc<double>(4);
-        epi = alloc<double>(2 * (dpad / 32) + 8);
+        epi = alloc<double>(2 * (dpad / 16) + 8);
         dots = alloc<double>(pmax + 4);
         Rinv = alloc<float>(pp);
         P = alloc<float>(pp);
@@ -352,8 +352,8 @@ lra_status Engine::cholqr2(float *W, int p) {
     LRA_CUDA(cudaMemsetAsync(ws_.status, 0, sizeof(int) * 2, s_));
     for (int pass = 0; pass < 2; ++pass) {
         gram(s_, W, dpad, 1, dpad, p, ws_.Gm, ws_.gscr);
-        chol_inv(s_, ws_.Gm, p, ws_.Rinv, ws_.status + pass);
-        apply_right(s_, W, dpad, 1, dpad, p, ws_.Rinv, p, ws_.T1, 1, dpad);
+        chol(s_, ws_.Gm, p, ws_.Rinv, ws_.status + pass);
+        trsm_rows(s_, W, dpad, dpad, p, ws_.Rinv, ws_.T1);
         LRA_CUDA(cudaMemcpyAsync(W, ws_.T1, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
     }
     int st[2];
@@ -366,11 +366,11 @@ lra_status Engine::cholqr2(float *W, int p) {
     return LRA_OK;
 }
 
-void Engine::ritz(const float *S, int p, bool use32) {
+void Engine::ritz(const float *S, int p, bool use32, int passes) {
     const int PP = pad_p(p);
     xt_mul(S, p, ws_.Q, use32);
     gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
-    sym_eig(s_, ws_.H, p, ws_.evals, ws_.evecs, ws_.eigwork);
+    sym_eig(s_, ws_.H, p, ws_.evals, ws_.evecs, ws_.eigwork, passes);
 }
 
 void Engine::normalize(float *z) {
@@ -618,7 +618,7 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     const int PP = pad_p(p);
     double *h = ws_.host;
     while (true) {
-        ritz(S, p, false);
+        ritz(S, p, false, 1);
         LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
         sync();
         double sk = 0.0;

@@ -161,7 +161,8 @@ class Engine {
     void inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
                const float *cval, int64_t m, double eta, double lam);
     lra_status cholqr2(float *W, int p);
-    void ritz(const float *S, int p, bool use32);  // -> ws.Q, ws.H, ws.evals, ws.evecs
+    // -> ws.Q, ws.H, ws.evals, ws.evecs; passes = FP64 refinement passes of the eigensolver
+    void ritz(const float *S, int p, bool use32, int passes = 2);
     void normalize(float *z);                      // one column, in place
     double dot1(const float *a, const float *b);   // host read
 

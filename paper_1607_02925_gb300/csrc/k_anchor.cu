@@ -286,27 +286,39 @@ __global__ void __launch_bounds__(256) xy_kernel(const TX *__restrict__ X, int64
 }
 
 // --- epilogue: M = lambda Wt - sum_c Gp[c] - B (or G only) -------------------
+// CTA = 16 rows x PP; four independent chunk accumulators per element, combined
+// in a fixed order (deterministic).
+constexpr int kER = 16;
+
 __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__ Gp, int nchunks,
                                                        int64_t dpad, int PP, int p, double lam,
                                                        const float *__restrict__ Wt,
                                                        const float *__restrict__ B,
                                                        float *__restrict__ out, int mode,
                                                        double *__restrict__ partial) {
-    extern __shared__ __align__(16) float tile[];  // [32][PP + 1]
+    extern __shared__ __align__(16) float tile[];  // [kER][PP + 1]
     __shared__ double red[2][8];
     const int tid = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int64_t r0 = (int64_t)blockIdx.x * kER;
     const int ts = PP + 1;
-    for (int e = tid; e < 32 * PP; e += 256) {
-        float acc = 0.0f;  // a few dozen chunk partials: FP32, fixed order
+    const int64_t stride = dpad * PP;
+    for (int e = tid; e < kER * PP; e += 256) {
         const int64_t off = r0 * PP + e;
-        for (int c = 0; c < nchunks; ++c) acc += Gp[(int64_t)c * dpad * PP + off];
-        tile[(e / PP) * ts + (e % PP)] = acc;
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        int c = 0;
+        for (; c + 3 < nchunks; c += 4) {
+            a0 += Gp[(c + 0) * stride + off];
+            a1 += Gp[(c + 1) * stride + off];
+            a2 += Gp[(c + 2) * stride + off];
+            a3 += Gp[(c + 3) * stride + off];
+        }
+        for (; c < nchunks; ++c) a0 += Gp[c * stride + off];
+        tile[(e / PP) * ts + (e % PP)] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     double m2 = 0.0, b2 = 0.0;
-    for (int e = tid; e < 32 * p; e += 256) {
-        const int r = e & 31, j = e >> 5;
+    for (int e = tid; e < kER * p; e += 256) {
+        const int r = e % kER, j = e / kER;
         const int64_t gi = (r0 + r) + (int64_t)j * dpad;
         const float g = tile[r * ts + j];
         if (mode == 0) {
@@ -436,8 +448,8 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
 void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
                      double *scratch) {
-    const int nb = (int)(dpad / 32);
-    const size_t smem = sizeof(float) * 32 * (PP + 1);
+    const int nb = (int)(dpad / kER);
+    const size_t smem = sizeof(float) * kER * (PP + 1);
     const int mode = (Wt != nullptr) ? 0 : 1;
     epilogue_kernel<<<nb, 256, smem, s>>>(Gp, nchunks, dpad, PP, p, lam, Wt, B, M, mode, scratch);
     LRA_LAUNCHED();

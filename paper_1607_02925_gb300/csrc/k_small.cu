@@ -110,12 +110,21 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, 
         a = b;
         b = t;
     }
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * p4 * p4 + a * p4 + b];
-    G[e] = s;
+    // four independent partial sums over interleaved parts, combined in a fixed order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const int64_t stride = (int64_t)p4 * p4, off = (int64_t)a * p4 + b;
+    int c = 0;
+    for (; c + 3 < nparts; c += 4) {
+        s0 += part[(c + 0) * stride + off];
+        s1 += part[(c + 1) * stride + off];
+        s2 += part[(c + 2) * stride + off];
+        s3 += part[(c + 3) * stride + off];
+    }
+    for (; c < nparts; ++c) s0 += part[c * stride + off];
+    G[e] = (s0 + s1) + (s2 + s3);
 }
 
-int gram_blocks(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, kGR), 2 * 152)); }
+int gram_blocks(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, kGR), 152)); }
 
 // ---------------------------------------------------------------------------
 // Cholesky G = L L^T (L = R^T) and L^-1, FP64, one CTA.  Rinv = (L^-1)^T as
@@ -174,6 +183,77 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double *__restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Cholesky G = L L^T in FP64, one CTA, one barrier per column: step c reads
+// column c (not yet scaled) and updates the trailing lower triangle; the
+// scaling of column c by its pivot is applied when R is written out.
+// R = L^T (upper, FP32 row-major); status = 1 if a pivot is not positive.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) chol_kernel(const double *__restrict__ G, int p,
+                                                   float *__restrict__ R, int *__restrict__ status) {
+    extern __shared__ __align__(16) double sl[];
+    const int ld = p + 1;
+    double *L = sl;           // [p][ld]
+    double *piv = sl + p * ld;  // [p]
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < p * p; e += nt) L[(e % p) * ld + e / p] = G[e];
+    __syncthreads();
+    for (int c = 0; c < p; ++c) {
+        double dd = L[c * ld + c];
+        // a pivot at the rounding level of its original diagonal means the
+        // columns are linearly dependent to working precision
+        if (!(dd > 1e-14 * G[c + (int64_t)c * p]) || !isfinite(dd)) {
+            if (tid == 0) bad = 1;
+            dd = 1.0;
+        }
+        if (tid == 0) piv[c] = sqrt(dd);
+        const double inv = 1.0 / dd;  // (l_rc / sqrt dd)(l_sc / sqrt dd) = l_rc l_sc / dd
+        const int m = p - c - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int r = e / m, s = e % m;
+            if (s <= r) {
+                const int rr = c + 1 + r, ss = c + 1 + s;
+                L[rr * ld + ss] -= L[rr * ld + c] * L[ss * ld + c] * inv;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < p * p; e += nt) {
+        const int a = e / p, b = e % p;  // R[a][b] = L[b][a] / piv[a] for b > a
+        float v = 0.0f;
+        if (b == a)
+            v = (float)piv[a];
+        else if (b > a)
+            v = (float)(L[b * ld + a] / piv[a]);
+        R[e] = v;
+    }
+    if (tid == 0) *status = bad;
+}
+
+// Q = W R^-1 row by row (forward substitution q_j = (w_j - sum_{l<j} q_l R_lj) / R_jj),
+// one thread per row; R in shared memory, the row's q in shared memory.
+__global__ void __launch_bounds__(128) trsm_rows_kernel(const float *__restrict__ W, int64_t rows,
+                                                        int64_t ld, int p, const float *__restrict__ R,
+                                                        float *__restrict__ Q) {
+    extern __shared__ __align__(16) float sr[];
+    float *Rs = sr;               // [p][p]
+    float *qs = sr + p * p;       // [p][128]
+    const int tid = threadIdx.x;
+    for (int e = tid; e < p * p; e += 128) Rs[e] = R[e];
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * 128 + tid;
+    if (r >= rows) return;
+    for (int j = 0; j < p; ++j) {
+        float s = W[r + (int64_t)j * ld];
+        for (int l = 0; l < j; ++l) s = fmaf(-qs[l * 128 + tid], Rs[l * p + j], s);
+        const float q = s / Rs[j * p + j];
+        qs[j * 128 + tid] = q;
+        Q[r + (int64_t)j * ld] = q;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Out (rows x q) = A (rows x p) T (p x q, FP32 row-major).  CTA = 128 rows x
 // 16 output columns; thread = one row x 8 columns.
 // ---------------------------------------------------------------------------
@@ -217,38 +297,50 @@ __global__ void __launch_bounds__(256) apply_right_kernel(const float *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Cyclic Jacobi (round-robin parallel ordering) in one CTA.  T = float: the
-// eigenvectors are FP32-accurate; eigenvalues are recomputed afterwards as FP64
-// Rayleigh quotients of the FP64 matrix.  Classical rotation (Golub & Van Loan,
-// sym.schur2): tau = (a_jj - a_ii) / (2 a_ij), t = sign(tau)/(|tau| + sqrt(1 +
-// tau^2)), c = 1/sqrt(1 + t^2), s = t c; A <- J^T A J, V <- V J.
+// Cyclic Jacobi in FP32, one CTA, round-robin ordering (p2 = p rounded up to
+// even; index m = p2 - 1 is the fixed player): in round r index a is paired
+// with a' = r if a = m, m if a = r, else (2r - a) mod m.  Classical rotation
+// (Golub & Van Loan, sym.schur2) for pair (i < j): tau = (a_jj - a_ii)/(2 a_ij),
+// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.  The
+// two-sided update A' = J^T A J and V' = V J of all disjoint pairs of a round is
+// computed elementwise into a second buffer:
+//   A'[a][b] = al_a (al_b A[a][b] + be_b A[a][b']) + be_a (al_b A[a'][b] + be_b A[a'][b'])
+// with (al, be) = (c, -s) for the smaller index of a pair, (c, +s) for the
+// larger; two barriers per round.
 // ---------------------------------------------------------------------------
-template <typename T>
+__device__ __forceinline__ int rr_partner(int a, int r, int m) {
+    if (a == m) return r;
+    if (a == r) return m;
+    int q = (2 * r - a) % m;
+    return q < 0 ? q + m : q;
+}
+
 __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ H, int p,
                                                      double *__restrict__ Vout, int max_sweeps) {
-    extern __shared__ __align__(16) unsigned char raw[];
+    extern __shared__ __align__(16) float jb[];
     const int p2 = p + (p & 1);
     const int ld = p2 + 1;
-    T *A = reinterpret_cast<T *>(raw);  // [p2][ld]
-    T *V = A + p2 * ld;                 // [p2][ld]
-    T *cs = V + p2 * ld;                // [p2/2]
-    T *sn = cs + p2 / 2;                // [p2/2]
-    int *pi = reinterpret_cast<int *>(sn + p2 / 2);  // [p2/2]
-    int *pj = pi + p2 / 2;
+    const int sz = p2 * ld;
+    float *A0 = jb, *A1 = jb + sz, *V0 = jb + 2 * sz, *V1 = jb + 3 * sz;
+    float *al = jb + 4 * sz;        // [p2] alpha of each index this round
+    float *be = al + p2;            // [p2] beta (-s for the smaller index, +s for the larger)
+    int *part = reinterpret_cast<int *>(be + p2);  // [p2] partner this round
     __shared__ double red_off[16], red_tot[16];
     __shared__ int stop, rotated;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const T eps = sizeof(T) == 4 ? (T)1e-7 : (T)1e-15;
+    const float eps = 1e-7f;
     if (tid == 0) rotated = 0;
     for (int e = tid; e < p2 * p2; e += nt) {
         const int a = e / p2, b = e % p2;
-        A[a * ld + b] = (a < p && b < p) ? (T)H[a + (int64_t)b * p] : (T)0;
-        V[a * ld + b] = (a == b) ? (T)1 : (T)0;
+        A0[a * ld + b] = (a < p && b < p) ? (float)H[a + (int64_t)b * p] : 0.0f;
+        V0[a * ld + b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    const int mrounds = p2 - 1;
+    const int m = p2 - 1;
+    const int tpr = nt / p2;          // threads per row in the update phase (>= 4)
+    const int row = tid / tpr, q = tid - (tid / tpr) * tpr;
+    float *A = A0, *An = A1, *V = V0, *Vn = V1;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        // convergence: off-diagonal mass vs total
         double off = 0.0, tot = 0.0;
         for (int e = tid; e < p2 * p2; e += nt) {
             const int a = e / p2, b = e % p2;
@@ -269,81 +361,55 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ 
                 o += red_off[w];
                 t += red_tot[w];
             }
-            // squared relative off-diagonal mass: FP32 sweeps stop at 1e-5 (the
-            // FP64 refinement that follows squares it twice); FP64 at 1e-14
-            const double tol = sizeof(T) == 4 ? 1e-10 : 1e-28;
-            stop = (o <= tol * t || (sweep > 0 && !rotated)) ? 1 : 0;
+            // squared relative off-diagonal mass 1e-10: the FP64 refinement that
+            // follows squares the remaining rotation angles
+            stop = (o <= 1e-10 * t || (sweep > 0 && !rotated)) ? 1 : 0;
             rotated = 0;
         }
         __syncthreads();
         if (stop) break;
-        for (int rnd = 0; rnd < mrounds; ++rnd) {
-            for (int k = tid; k < p2 / 2; k += nt) {
-                int i, j;
-                if (k == 0) {
-                    i = rnd;
-                    j = mrounds;
-                } else {
-                    i = (rnd + k) % mrounds;
-                    j = (rnd - k + mrounds) % mrounds;
-                }
-                if (i > j) {
-                    const int t = i;
-                    i = j;
-                    j = t;
-                }
-                pi[k] = i;
-                pj[k] = j;
-                const T aij = A[i * ld + j];
-                const T aii = A[i * ld + i], ajj = A[j * ld + j];
-                T c = (T)1, s = (T)0;
-                if (aij != (T)0 && fabs(aij) > eps * sqrt(fabs(aii * ajj))) {
-                    const T tau = (ajj - aii) / ((T)2 * aij);
-                    T t;
-                    if (fabs(tau) > (T)1e15)
-                        t = (T)1 / ((T)2 * tau);
-                    else
-                        t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
-                    c = (T)1 / sqrt((T)1 + t * t);
-                    s = t * c;
-                    rotated = 1;
-                }
-                cs[k] = c;
-                sn[k] = s;
-            }
-            __syncthreads();
-            // columns: A <- A J, V <- V J
-            for (int e = tid; e < (p2 / 2) * p2; e += nt) {
-                const int k = e / p2, l = e % p2;
-                const T c = cs[k], s = sn[k];
-                if (s == (T)0) continue;
-                const int i = pi[k], j = pj[k];
-                const T ai = A[l * ld + i], aj = A[l * ld + j];
-                A[l * ld + i] = c * ai - s * aj;
-                A[l * ld + j] = s * ai + c * aj;
-                const T vi = V[l * ld + i], vj = V[l * ld + j];
-                V[l * ld + i] = c * vi - s * vj;
-                V[l * ld + j] = s * vi + c * vj;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int e = tid; e < (p2 / 2) * p2; e += nt) {
-                const int k = e / p2, l = e % p2;
-                const T c = cs[k], s = sn[k];
-                if (s == (T)0) continue;
-                const int i = pi[k], j = pj[k];
-                const T ai = A[i * ld + l], aj = A[j * ld + l];
-                A[i * ld + l] = c * ai - s * aj;
-                A[j * ld + l] = s * ai + c * aj;
-            }
-            __syncthreads();
-            for (int k = tid; k < p2 / 2; k += nt) {
-                if (sn[k] != (T)0) {
-                    A[pi[k] * ld + pj[k]] = (T)0;
-                    A[pj[k] * ld + pi[k]] = (T)0;
+        for (int r = 0; r < m; ++r) {
+            // phase 1: partner, and the (alpha, beta) of each index for this round
+            for (int i = tid; i < p2; i += nt) {
+                const int j = rr_partner(i, r, m);
+                part[i] = j;
+                if (i < j) {
+                    const float aij = A[i * ld + j], aii = A[i * ld + i], ajj = A[j * ld + j];
+                    float c = 1.0f, s = 0.0f;
+                    if (aij != 0.0f && fabsf(aij) > eps * sqrtf(fabsf(aii * ajj))) {
+                        const float tau = (ajj - aii) / (2.0f * aij);
+                        const float t = fabsf(tau) > 1e15f ? 1.0f / (2.0f * tau)
+                                                             : copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                        c = 1.0f / sqrtf(1.0f + t * t);
+                        s = t * c;
+                        rotated = 1;
+                    }
+                    al[i] = c;
+                    al[j] = c;
+                    be[i] = -s;
+                    be[j] = s;
                 }
             }
             __syncthreads();
+            // phase 2: A' = J^T A J and V' = V J elementwise into the other buffers
+            // thread = (row a, column offset q): columns q, q + tpr, ... of row a
+            if (row < p2) {
+                const int a = row, ap = part[a];
+                const float ala = al[a], bea = be[a];
+                const float *Aa = A + a * ld, *Aap = A + ap * ld, *Va = V + a * ld;
+                float *Ana = An + a * ld, *Vna = Vn + a * ld;
+                for (int b = q; b < p2; b += tpr) {
+                    const int bp = part[b];
+                    const float alb = al[b], beb = be[b];
+                    const float x = alb * Aa[b] + beb * Aa[bp];
+                    const float y = alb * Aap[b] + beb * Aap[bp];
+                    Ana[b] = (bp == a && beb != 0.0f) ? 0.0f : ala * x + bea * y;
+                    Vna[b] = alb * Va[b] + beb * Va[bp];
+                }
+            }
+            __syncthreads();
+            float *t = A; A = An; An = t;
+            t = V; V = Vn; Vn = t;
         }
     }
     for (int e = tid; e < p * p; e += nt) {
@@ -528,6 +594,21 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
     LRA_LAUNCHED();
 }
 
+void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
+    const size_t smem = sizeof(double) * ((size_t)p * (p + 1) + p);
+    LRA_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nt = p <= 48 ? 128 : 256;
+    chol_kernel<<<1, nt, smem, s>>>(G, p, R, status);
+    LRA_LAUNCHED();
+}
+
+void trsm_rows(cudaStream_t s, const float *W, int64_t rows, int64_t ld, int p, const float *R, float *Q) {
+    const size_t smem = sizeof(float) * ((size_t)p * p + (size_t)p * 128);
+    LRA_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    trsm_rows_kernel<<<(unsigned)ceil_div(rows, 128), 128, smem, s>>>(W, rows, ld, p, R, Q);
+    LRA_LAUNCHED();
+}
+
 void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status) {
     const size_t smem = sizeof(double) * 2 * p * (p + 1);
     LRA_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -548,7 +629,7 @@ void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int6
 // Newton-Schulz orthonormalisation V <- V (3 I - V^T V) / 2, B = V^T H V, the
 // first-order rotation V <- V (I + E) that annihilates B's off-diagonal to
 // second order, a second orthonormalisation, and FP64 Rayleigh quotients.
-void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work) {
+void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes) {
     const int p2 = p + (p & 1);
     const size_t pp = (size_t)p * p;
     double *V = work;           // p*p
@@ -556,9 +637,10 @@ void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evec
     double *T1 = evecs;         // scratch until the final sort (p*p)
     double *T2 = work + pp + p;  // p*p
     double *V2 = T2 + pp;       // p*p
-    const size_t smem = sizeof(float) * (2 * p2 * (p2 + 1) + p2) + sizeof(int) * p2;
-    LRA_CUDA(cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    jacobi_kernel<float><<<1, 512, smem, s>>>(H, p, V, 40);
+    const size_t smem = sizeof(float) * (4 * p2 * (p2 + 1) + 3 * p2);
+    LRA_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nt = p2 <= 16 ? 128 : 512;
+    jacobi_kernel<<<1, nt, smem, s>>>(H, p, V, 40);
     LRA_LAUNCHED();
     auto gemm = [&](const double *A, const double *B, int ta, double alpha, double beta, double *C) {
         gemm_pp_kernel<<<p, 128, 0, s>>>(A, B, p, ta, alpha, beta, C);
@@ -568,7 +650,7 @@ void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evec
         gemm(Vin, Vin, 1, -0.5, 1.5, T1);   // T1 = 1.5 I - 0.5 V^T V
         gemm(Vin, T1, 0, 1.0, 0.0, Vout);   // Vout = V T1
     };
-    for (int pass = 0; pass < 2; ++pass) {  // each pass squares the off-diagonal
+    for (int pass = 0; pass < passes; ++pass) {  // each pass squares the off-diagonal
         orthonormalise(V, V2);
         gemm(H, V2, 0, 1.0, 0.0, T1);       // T1 = H V
         gemm(V2, T1, 1, 1.0, 0.0, T2);      // T2 = V^T H V

@@ -82,13 +82,18 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
 // Cholesky G = R^T R (upper R), Rinv = R^-1 as FP32 p x p row-major;
 // status[0] = 0 ok / 1 not positive definite
 void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status);
+// Cholesky G = R^T R in FP64 (one barrier per column); R upper FP32 row-major
+void chol(cudaStream_t s, const double *G, int p, float *R, int *status);
+// Q = W R^-1 by row-wise forward substitution (W, Q rows x p column-major)
+void trsm_rows(cudaStream_t s, const float *W, int64_t rows, int64_t ld, int p, const float *R, float *Q);
 // Out (rows x q) = A (rows x p) T (p x q, FP32 row-major); strides for A and Out
 void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int64_t acs, int p,
                  const float *T, int q, float *Out, int64_t ors, int64_t ocs);
 // Symmetric eigendecomposition of H (p x p FP64 column-major); evals desc,
 // evecs column-major FP64 (largest |entry| positive).  work >= sym_eig_work(p) doubles.
 int64_t sym_eig_work(int p);
-void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work);
+// passes: FP64 refinement passes after the FP32 sweeps (each squares the residual rotation)
+void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes = 2);
 // P (p x p FP32 row-major) = V_k diag(f(rho)) V_k^T with f = 1/(lam - rho):
 // the Galerkin inverse (lam I - H)^-1 on the Ritz basis.  kcols = p.
 void ritz_inverse(cudaStream_t s, const double *evecs, const double *evals, int p, double lam,
