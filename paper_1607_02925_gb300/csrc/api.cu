@@ -2,6 +2,8 @@
 // conversion between the caller's layouts (leading dimension d) and the
 // library's padded device layouts, and error-status translation.
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "engine.h"
@@ -15,6 +17,19 @@ static thread_local int64_t g_launches = 0;
 void set_error(const std::string &msg) { g_last_error = msg; }
 void count_launch() { ++g_launches; }
 int64_t launches_of_thread() { return g_launches; }
+
+void ensure_smem(const void *kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> limit;  // (device, kernel) -> bytes set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    int &cur = limit[{dev, kernel}];
+    if (bytes > cur) {
+        LRA_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        cur = bytes;
+    }
+}
 
 }  // namespace lra
 

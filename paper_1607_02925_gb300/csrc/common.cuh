@@ -47,6 +47,15 @@ struct Error {
 void count_launch();
 int64_t launches_of_thread();
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// attribute is per function and shared by all threads, so it is only ever
+// raised: a concurrent launch needing less is still covered.
+void ensure_smem(const void *kernel, int bytes);
+template <typename K>
+inline void ensure_smem(K *kernel, int bytes) {
+    ensure_smem(reinterpret_cast<const void *>(kernel), bytes);
+}
+
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea, Flood 2014): state += gamma; out = mix64(state).
 // The t-th word of the stream with key K is mix64(K + gamma (t + 1)).

@@ -11,7 +11,7 @@
 
 namespace lra {
 
-void *dev_alloc(lra_ctx *ctx, size_t bytes) {
+void *dev_alloc(lra_ctx *ctx, size_t bytes, cudaStream_t s) {
     if (ctx->budget) {
         const size_t now = ctx->used.fetch_add(bytes) + bytes;
         if (now > ctx->budget) {
@@ -23,7 +23,7 @@ void *dev_alloc(lra_ctx *ctx, size_t bytes) {
         ctx->used.fetch_add(bytes);
     }
     void *p = nullptr;
-    const cudaError_t e = cudaMalloc(&p, bytes);
+    const cudaError_t e = s ? cudaMallocAsync(&p, bytes, s) : cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         ctx->used.fetch_sub(bytes);
         cudaGetLastError();
@@ -33,9 +33,12 @@ void *dev_alloc(lra_ctx *ctx, size_t bytes) {
     return p;
 }
 
-void dev_free(lra_ctx *ctx, void *p, size_t bytes) {
+void dev_free(lra_ctx *ctx, void *p, size_t bytes, cudaStream_t s) {
     if (!p) return;
-    cudaFree(p);
+    if (s)
+        cudaFreeAsync(p, s);
+    else
+        cudaFree(p);
     ctx->used.fetch_sub(bytes);
 }
 
@@ -90,8 +93,14 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax) {
     return b;
 }
 
-Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
-    : ctx(c), dpad(dpad_), n(n_), pmax(pmax_), PPmax(pad_p(pmax_)) {
+Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream)
+    : ctx(c), dpad(dpad_), n(n_), pmax(pmax_), PPmax(pad_p(pmax_)), astream(alloc_stream) {
+    auto zero = [&](void *p, size_t bytes) {
+        if (astream)
+            LRA_CUDA(cudaMemsetAsync(p, 0, bytes, astream));
+        else
+            LRA_CUDA(cudaMemset(p, 0, bytes));
+    };
     try {
         const size_t blk = (size_t)dpad * pmax;
         S = alloc<float>(blk);
@@ -103,8 +112,8 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
         Wr = alloc<float>((size_t)dpad * PPmax);
         Q = alloc<float>((size_t)n * PPmax);
         Y = alloc<float>((size_t)n * PPmax);
-        LRA_CUDA(cudaMemset(Q, 0, sizeof(float) * n * PPmax));
-        LRA_CUDA(cudaMemset(Y, 0, sizeof(float) * n * PPmax));
+        zero(Q, sizeof(float) * n * PPmax);
+        zero(Y, sizeof(float) * n * PPmax);
         nchunks = xy_chunks(dpad, n);
         Gp = alloc<float>((size_t)nchunks * dpad * PPmax);
         const size_t pp = (size_t)pmax * pmax;
@@ -121,36 +130,40 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_)
         P = alloc<float>(pp);
         status = alloc<int>(4);
         tcerr = alloc<int>(4);
-        LRA_CUDA(cudaMemset(tcerr, 0, sizeof(int) * 4));
+        zero(tcerr, sizeof(int) * 4);
         ldy = tc_ldy(n);
         Wb = alloc<__nv_bfloat16>((size_t)2 * PPmax * dpad);
         Yb = alloc<__nv_bfloat16>((size_t)2 * PPmax * ldy);
         LRA_CUDA(cudaMallocHost(&host, sizeof(double) * (2 * pmax + 16)));
     } catch (...) {
-        for (auto &a : allocs) dev_free(ctx, a.first, a.second);
+        for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
         allocs.clear();
         throw;
     }
 }
 
 Workspace::~Workspace() {
-    for (auto &a : allocs) dev_free(ctx, a.first, a.second);
-    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap);
-    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap);
+    if (astream) cudaStreamSynchronize(astream);
+    for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
+    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap, astream);
+    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap, astream);
+    if (astream) cudaStreamSynchronize(astream);
     if (host) cudaFreeHost(host);
 }
 
 void Workspace::ensure_idx(int64_t m) {
     if (m <= idx_cap) return;
     const int64_t cap = std::max<int64_t>(m, 2 * idx_cap);
-    cudaDeviceSynchronize();
-    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap);
-    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap);
+    // stream-ordered frees wait for the stream's earlier work; plain frees need
+    // the device idle first
+    if (!astream) cudaDeviceSynchronize();
+    if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap, astream);
+    if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap, astream);
     idx = nullptr;
     cval = nullptr;
     idx_cap = 0;
-    idx = static_cast<int32_t *>(dev_alloc(ctx, sizeof(int32_t) * cap));
-    cval = static_cast<float *>(dev_alloc(ctx, sizeof(float) * cap));
+    idx = static_cast<int32_t *>(dev_alloc(ctx, sizeof(int32_t) * cap, astream));
+    cval = static_cast<float *>(dev_alloc(ctx, sizeof(float) * cap, astream));
     idx_cap = cap;
 }
 
@@ -231,7 +244,7 @@ const lra_mat::Table &Engine::ensure_table(int mode) {
         t.c = static_cast<float *>(dev_alloc(mat_->ctx, sizeof(float) * n));
     }
     const int64_t scr = std::max<int64_t>(ceil_div(n, 1024) + 16, ceil_div(n, 256) + 16);
-    uint64_t *scratch = static_cast<uint64_t *>(dev_alloc(mat_->ctx, sizeof(uint64_t) * scr));
+    uint64_t *scratch = static_cast<uint64_t *>(dev_alloc(mat_->ctx, sizeof(uint64_t) * scr, s_));
     double *kap = reinterpret_cast<double *>(mat_->dev_sm) + 2;
     try {
         sampling_table(s_, mat_->norm2, n, mode, mat_->dev_sm + 1, t.cum, t.c, kap, scratch);
@@ -245,10 +258,10 @@ const lra_mat::Table &Engine::ensure_table(int mode) {
         t.ok = true;
     } catch (...) {
         cudaStreamSynchronize(s_);
-        dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr);
+        dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr, s_);
         throw;
     }
-    dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr);
+    dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr, s_);
     if (t.total == 0) {
         set_error("X has no non-zero column");
         throw Error{LRA_EINVAL};

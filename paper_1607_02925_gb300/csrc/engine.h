@@ -54,9 +54,9 @@ struct lra_mat {
 
 namespace lra {
 
-// Device allocation charged to a context's budget.
-void *dev_alloc(lra_ctx *ctx, size_t bytes);
-void dev_free(lra_ctx *ctx, void *p, size_t bytes);
+// Device allocation charged to a context's budget (stream-ordered when s != nullptr).
+void *dev_alloc(lra_ctx *ctx, size_t bytes, cudaStream_t s = nullptr);
+void dev_free(lra_ctx *ctx, void *p, size_t bytes, cudaStream_t s = nullptr);
 
 struct Opts {
     int shift_policy = LRA_SHIFT_PAPER;
@@ -130,13 +130,17 @@ struct Workspace {
     double *host = nullptr;  // pinned readback area
     std::vector<std::pair<void *, size_t>> allocs;
 
-    Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_);
+    // astream != nullptr: buffers come from the stream-ordered allocator on that
+    // stream (no device-wide synchronisation on free; used by the request loop)
+    cudaStream_t astream = nullptr;
+
+    Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream = nullptr);
     ~Workspace();
     void ensure_idx(int64_t m);
     template <typename T>
     T *alloc(size_t count) {
         const size_t bytes = std::max<size_t>(16, sizeof(T) * count);
-        void *p = dev_alloc(ctx, bytes);
+        void *p = dev_alloc(ctx, bytes, astream);
         allocs.emplace_back(p, bytes);
         return static_cast<T *>(p);
     }

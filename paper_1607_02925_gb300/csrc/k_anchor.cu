@@ -407,11 +407,11 @@ void xtw(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad,
         const dim3 grid((unsigned)ceil_div(n, kTI));
         if (dt == LRA_BF16) {
             auto k = xtw_kernel<__nv_bfloat16, P>;
-            LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(k, (int)smem);
             k<<<grid, 256, smem, s>>>((const __nv_bfloat16 *)X, ldx, dpad, n, Wr, Y);
         } else {
             auto k = xtw_kernel<float, P>;
-            LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(k, (int)smem);
             k<<<grid, 256, smem, s>>>((const float *)X, ldx, dpad, n, Wr, Y);
         }
         LRA_LAUNCHED();
@@ -434,11 +434,11 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
         const dim3 grid((unsigned)(dpad / kTR), (unsigned)nchunks);
         if (dt == LRA_BF16) {
             auto k = xy_kernel<__nv_bfloat16, P>;
-            LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(k, (int)smem);
             k<<<grid, 256, smem, s>>>((const __nv_bfloat16 *)X, ldx, dpad, n, Y, Gp, cpc);
         } else {
             auto k = xy_kernel<float, P>;
-            LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(k, (int)smem);
             k<<<grid, 256, smem, s>>>((const float *)X, ldx, dpad, n, Y, Gp, cpc);
         }
         LRA_LAUNCHED();

@@ -401,7 +401,7 @@ void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
         auto launch = [&](auto kern, int smem) {
-            LRA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            ensure_smem(kern, (int)smem);
             kern<<<(unsigned)ceil_div(n, kBM), 128, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
             LRA_LAUNCHED();
         };
@@ -422,7 +422,7 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
         constexpr int P = decltype(ppc)::value;
         const dim3 grid((unsigned)(dpad / kBM), (unsigned)nchunks);
         auto launch = [&](auto kern, int smem) {
-            LRA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            ensure_smem(kern, (int)smem);
             kern<<<grid, 128, smem, s>>>(mx, mxl, my, cpc, n, dpad, Gp, err);
             LRA_LAUNCHED();
         };

@@ -159,7 +159,7 @@ void launch_inner(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int
                   float eta, float lam, int nt) {
     auto k = svrg_inner_kernel<TX, S, PC>;
     const size_t smem = (size_t)kRing * dpad * sizeof(TX);
-    LRA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem(k, (int)smem);
     const unsigned grid = (unsigned)ceil_div(p, PC);
     k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
     LRA_LAUNCHED();

@@ -596,7 +596,7 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
 
 void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
     const size_t smem = sizeof(double) * ((size_t)p * (p + 1) + p);
-    LRA_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem(chol_kernel, (int)smem);
     const int nt = p <= 48 ? 128 : 256;
     chol_kernel<<<1, nt, smem, s>>>(G, p, R, status);
     LRA_LAUNCHED();
@@ -604,14 +604,14 @@ void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
 
 void trsm_rows(cudaStream_t s, const float *W, int64_t rows, int64_t ld, int p, const float *R, float *Q) {
     const size_t smem = sizeof(float) * ((size_t)p * p + (size_t)p * 128);
-    LRA_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem(trsm_rows_kernel, (int)smem);
     trsm_rows_kernel<<<(unsigned)ceil_div(rows, 128), 128, smem, s>>>(W, rows, ld, p, R, Q);
     LRA_LAUNCHED();
 }
 
 void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status) {
     const size_t smem = sizeof(double) * 2 * p * (p + 1);
-    LRA_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem(chol_inv_kernel, (int)smem);
     chol_inv_kernel<<<1, 256, smem, s>>>(G, p, Rinv, status);
     LRA_LAUNCHED();
 }
@@ -638,7 +638,7 @@ void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evec
     double *T2 = work + pp + p;  // p*p
     double *V2 = T2 + pp;       // p*p
     const size_t smem = sizeof(float) * (4 * p2 * (p2 + 1) + 3 * p2);
-    LRA_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem(jacobi_kernel, (int)smem);
     const int nt = p2 <= 16 ? 128 : 512;
     jacobi_kernel<<<1, nt, smem, s>>>(H, p, V, 40);
     LRA_LAUNCHED();
