@@ -46,6 +46,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-outer", type=int, default=4)
+    ap.add_argument("--serve", action="store_true", help="request-loop benchmark instead")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-mean-ms", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -373,8 +376,145 @@ def run_lra(args):
     return 0
 
 
+def run_serve(args):
+    """Request-loop benchmark: a Poisson stream of rank-k requests of uneven
+    d, n, k and storage type served by lra_submit / lra_poll, against the same
+    stream run one job at a time with FP32 storage through lra_solve."""
+    import threading
+
+    import torch
+    import paper_1607_02925_gb300 as lra
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    rng = np.random.default_rng(5)
+    nreq = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(args.serve_mean_ms / 1e3, size=nreq))
+    reqs = []
+    for j in range(nreq):
+        r = np.random.default_rng(5_000_000 + j)
+        reqs.append(dict(d=int(r.choice([256, 1024, 4096])), n=int(r.choice([8192, 65536, 262144])),
+                         k=int(r.choice([5, 10, 20, 50])), bf16=bool(r.random() < 0.5)))
+    # device-resident pool of planted matrices, one per (d, n, k)
+    pool = {}
+    for d in (256, 1024, 4096):
+        for n in (8192, 65536, 262144):
+            ks = sorted({q["k"] for q in reqs if q["d"] == d and q["n"] == n})
+            if not ks:
+                continue
+            g = torch.Generator(device=dev)
+            g.manual_seed(d * 1000 + n)
+            qu, ru = torch.linalg.qr(torch.randn(d, d, generator=g, device=dev))
+            qu = qu * torch.sign(torch.diagonal(ru))[None, :]
+            qv, rv = torch.linalg.qr(torch.randn(n, d, generator=g, device=dev))
+            qv = qv * torch.sign(torch.diagonal(rv))[None, :]
+            for k in ks:
+                sig = torch.as_tensor(L.sigma_serving(k, d), device=dev, dtype=torch.float32)
+                pool[(d, n, k)] = (qv @ (qu * sig[None, :]).T).contiguous()   # (n, d) = X column-major
+            del qu, ru, qv, rv
+    torch.cuda.synchronize()
+    opt = lra.options(shift_policy=lra.LRA_SHIFT_FAR)
+
+    def make(ctx, q, storage):
+        X = pool[(q["d"], q["n"], q["k"])]
+        return lra.lra_create_dense(ctx, q["d"], q["n"], lra.LRA_F32, X, q["d"], True, storage)
+
+    # ---- served: continuous batching
+    ctx = lra.lra_init(local)
+    t0 = time.perf_counter()
+    done_t = [None] * nreq
+    results = [None] * nreq
+    outstanding = {}
+    lock = threading.Lock()
+
+    def submitter():
+        for j, q in enumerate(reqs):
+            wait = t0 + arrivals[j] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            m = make(ctx, q, lra.LRA_BF16 if q["bf16"] else lra.LRA_F32)
+            jid = lra.lra_submit(ctx, m, q["k"], 2 * q["k"], args.eps, 1000 + j, opt)
+            with lock:
+                outstanding[jid] = (j, m)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    finished = 0
+    while finished < nreq:
+        with lock:
+            items = list(outstanding.items())
+        progressed = False
+        for jid, (j, m) in items:
+            q = reqs[j]
+            U = torch.empty(q["k"], q["d"], device=dev)
+            r = torch.empty(q["k"], dtype=torch.float64, device=dev)
+            st = lra.lra_poll(ctx, jid, 0, U, r, allow=(4, 7, 8))
+            if st in (7, 8):
+                continue
+            done_t[j] = time.perf_counter() - t0
+            results[j] = (st, U.cpu().numpy(), r.cpu().numpy())
+            with lock:
+                del outstanding[jid]
+            lra.lra_mat_destroy(m)
+            finished += 1
+            progressed = True
+        if not progressed:
+            time.sleep(0.0005)
+    th.join()
+    lat = np.array(done_t) - arrivals
+    span = max(done_t) - arrivals[0]
+    # sampled results re-run alone must be bitwise equal
+    check = list(range(0, nreq, max(1, nreq // 10)))[:10]
+    equal = 0
+    for j in check:
+        q = reqs[j]
+        m = make(ctx, q, lra.LRA_BF16 if q["bf16"] else lra.LRA_F32)
+        U = torch.empty(q["k"], q["d"], device=dev)
+        r = torch.empty(q["k"], dtype=torch.float64, device=dev)
+        lra.lra_solve(m, q["k"], 2 * q["k"], args.eps, 1000 + j, opt, U, r)
+        lra.lra_mat_destroy(m)
+        equal += int(np.array_equal(U.cpu().numpy(), results[j][1]) and np.array_equal(r.cpu().numpy(), results[j][2]))
+    lra.lra_finalize(ctx)
+
+    # ---- baseline: one job at a time, FP32 storage, same arrival times
+    ctx = lra.lra_init(local)
+    tb = 0.0
+    blat = []
+    for j, q in enumerate(reqs):
+        start = max(tb, arrivals[j])
+        ts = time.perf_counter()
+        m = make(ctx, q, lra.LRA_F32)
+        U = torch.empty(q["k"], q["d"], device=dev)
+        r = torch.empty(q["k"], dtype=torch.float64, device=dev)
+        lra.lra_solve(m, q["k"], 2 * q["k"], args.eps, 1000 + j, opt, U, r)
+        lra.lra_mat_destroy(m)
+        tb = start + (time.perf_counter() - ts)
+        blat.append(tb - arrivals[j])
+    lra.lra_finalize(ctx)
+    blat = np.array(blat)
+    line = {
+        "metric": "serve_latency", "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "requests": nreq, "mean_interarrival_ms": args.serve_mean_ms,
+        "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+        "jobs_per_s": nreq / span, "bitwise_equal_alone": f"{equal}/{len(check)}",
+        "statuses": sorted({int(r[0]) for r in results}),
+        "baseline_one_at_a_time_f32": {"p50": float(np.percentile(blat, 50)),
+                                        "p99": float(np.percentile(blat, 99)),
+                                        "jobs_per_s": nreq / (tb - arrivals[0])},
+        "config": {"workload": "planted small-gap spectrum rescaled to k; d in {256,1024,4096}, "
+                               "n in {8192,65536,262144}, k in {5,10,20,50}, p = 2k, FP32/BF16 1:1",
+                   "shift": "far", "eps": args.eps, "slots": int(os.environ.get("LRA_SERVE_SLOTS", "8"))},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_lra(args)
