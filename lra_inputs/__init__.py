@@ -175,14 +175,18 @@ def planted_torch(d: int, n: int, sigma: np.ndarray, seed: int, device="cpu",
 # Sparse term-document-like matrix
 # ----------------------------------------------------------------------------
 
-def zipf_csr(d: int, n: int, seed: int, mean_nnz: float = 100.0, zipf_s: float = 1.1):
+def zipf_csr(d: int, n: int, seed: int, mean_nnz: float = 100.0, zipf_s: float = 1.1,
+             chunk: int = 16384):
     """Sparse X (d x n) with Zipf(s) row ids, returned in CSR of X (d rows).
 
-    Column j holds c_j = 1 + Poisson(mean_nnz - 1) distinct rows drawn from a
-    Zipf(s) law over 1..d (repeats rejected, no row permutation); its values are
-    ln(2 + Poisson(2)) and the column is then L2-normalised.
-    Returns (rowptr int64[d+1], colidx int32[nnz], val float32[nnz]) with column
-    indices sorted within each row.
+    Column j holds c_j = 1 + Poisson(mean_nnz - 1) distinct rows (at most d),
+    drawn from a Zipf(s) law over 1..d one after another with repeats rejected
+    (no row permutation): the column keeps the first c_j distinct rows of its
+    draw sequence.  Its values are ln(2 + Poisson(2)) and the column is then
+    L2-normalised.  Columns are generated in chunks of `chunk`, each from one
+    draw block of the seeded generator, so the output depends only on the
+    arguments.  Returns (rowptr int64[d+1], colidx int32[nnz], val float32[nnz])
+    with column indices sorted within each row.
     """
     rng = np.random.default_rng(seed)
     ranks = np.arange(1, d + 1, dtype=np.float64)
@@ -190,30 +194,46 @@ def zipf_csr(d: int, n: int, seed: int, mean_nnz: float = 100.0, zipf_s: float =
     pmf /= pmf.sum()
     cdf = np.cumsum(pmf)
     cdf[-1] = 1.0
-    cnt = 1 + rng.poisson(mean_nnz - 1.0, size=n)
-    cnt = np.minimum(cnt, d)
-    rows_all = np.empty(int(cnt.sum()), dtype=np.int32)
-    vals_all = np.empty(int(cnt.sum()), dtype=np.float32)
-    cols_all = np.repeat(np.arange(n, dtype=np.int32), cnt)
-    pos = 0
-    for j in range(n):
-        c = int(cnt[j])
-        chosen: list[int] = []
-        seen = set()
-        while len(chosen) < c:
-            draw = np.searchsorted(cdf, rng.random(2 * (c - len(chosen)) + 4), side="right")
-            for rr in draw:
-                rr = int(min(rr, d - 1))
-                if rr not in seen:
-                    seen.add(rr)
-                    chosen.append(rr)
-                    if len(chosen) == c:
-                        break
-        v = np.log(2.0 + rng.poisson(2.0, size=c))
-        v /= np.sqrt(np.sum(v * v))
-        rows_all[pos:pos + c] = chosen
-        vals_all[pos:pos + c] = v.astype(np.float32)
-        pos += c
+    cnt = np.minimum(1 + rng.poisson(mean_nnz - 1.0, size=n), d).astype(np.int64)
+    rows_parts, cols_parts = [], []
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        need = cnt[c0:c1]
+        got_rows = [None] * (c1 - c0)
+        todo = np.arange(c1 - c0)
+        budget = 2 * need + 16
+        while todo.size:
+            nd = budget[todo]
+            col = np.repeat(todo, nd)
+            row = np.minimum(np.searchsorted(cdf, rng.random(int(nd.sum())), side="right"), d - 1)
+            # first occurrence of each (column, row) in draw order
+            key = col.astype(np.int64) * d + row
+            _, first = np.unique(key, return_index=True)
+            first.sort()
+            col_f, row_f = col[first], row[first]
+            # rank of each distinct draw within its column, in draw order
+            starts = np.searchsorted(col_f, todo)
+            rank = np.arange(col_f.size) - np.repeat(starts, np.diff(np.append(starts, col_f.size)))
+            have = np.diff(np.append(starts, col_f.size))
+            ok = have >= need[todo]
+            keep = rank < need[col_f]
+            sel = keep & ok[np.searchsorted(todo, col_f)]
+            rr, cc = row_f[sel], col_f[sel]
+            bounds = np.searchsorted(cc, todo[ok])
+            ends = np.append(bounds[1:], cc.size)
+            for t, b, e in zip(todo[ok], bounds, ends):
+                got_rows[t] = rr[b:e]
+            todo = todo[~ok]
+            budget[todo] *= 2
+        for t in range(c1 - c0):
+            rows_parts.append(got_rows[t])
+            cols_parts.append(np.full(got_rows[t].size, c0 + t, dtype=np.int32))
+    rows_all = np.concatenate(rows_parts).astype(np.int32)
+    cols_all = np.concatenate(cols_parts)
+    v = np.log(2.0 + rng.poisson(2.0, size=rows_all.size))
+    colptr = np.concatenate(([0], np.cumsum(cnt)))
+    nrm = np.sqrt(np.add.reduceat(v * v, colptr[:-1]))
+    vals_all = (v / np.repeat(nrm, cnt)).astype(np.float32)
     order = np.lexsort((cols_all, rows_all))
     rows_s = rows_all[order]
     colidx = cols_all[order]

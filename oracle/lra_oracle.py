@@ -544,14 +544,22 @@ class Result:
 
 
 def outer_stop(E: list, eps: float, ell: int, min_outer: int) -> bool:
-    """Stop when the predicted remaining decrease of E is <= (eps/4) E_l:
-    r = clamp((E_{l-1}-E_l)/(E_{l-2}-E_{l-1}), 0, .99) (r = .99 when the earlier
-    difference is not positive), remaining = max(E_{l-1}-E_l, 0) r/(1-r)."""
+    """Stop when the predicted remaining decrease of E is <= (eps/4) E_l.
+
+    With differences D_j = E_{j-1} - E_j, the rate is the geometric mean over
+    the last w <= 4 of them, r = clamp((D_l / D_{l-w})^(1/w), 0, .99) (r = .99
+    when D_{l-w} is not positive), and remaining = max(D_l, 0) r / (1 - r)."""
     if ell + 1 < max(3, min_outer):
         return False
+    w = min(4, len(E) - 2)
     d1 = E[-2] - E[-1]
-    d0 = E[-3] - E[-2]
-    r = d1 / d0 if d0 > 0 else 0.99
+    d0 = E[-2 - w] - E[-1 - w]
+    if d0 > 0 and d1 > 0:
+        r = (d1 / d0) ** (1.0 / w)
+    elif d0 > 0:
+        r = 0.0
+    else:
+        r = 0.99
     r = min(max(r, 0.0), 0.99)
     remaining = max(d1, 0.0) * r / (1.0 - r)
     return remaining <= 0.25 * eps * E[-1]

@@ -89,7 +89,8 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax) {
     b += sizeof(float) * dpad * PP;             // Wr
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
-    b += sizeof(double) * (8 * pmax * pmax + gram_scratch(pmax) + dpad);
+    b += sizeof(double) * (9 * pmax * pmax + gram_scratch(pmax) + dpad);
+    b += 2 * sizeof(__nv_bfloat16) * PP * (dpad + tc_ldy(n));  // Wb Yb
     return b;
 }
 
@@ -118,6 +119,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         Gp = alloc<float>((size_t)nchunks * dpad * PPmax);
         const size_t pp = (size_t)pmax * pmax;
         H = alloc<double>(pp);
+        Hc = alloc<double>(pp);
         evals = alloc<double>(pmax);
         evecs = alloc<double>(pp);
         eigwork = alloc<double>(sym_eig_work(pmax));
@@ -383,7 +385,14 @@ void Engine::ritz(const float *S, int p, bool use32, int passes) {
     const int PP = pad_p(p);
     xt_mul(S, p, ws_.Q, use32);
     gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
-    sym_eig(s_, ws_.H, p, ws_.evals, ws_.evecs, ws_.eigwork, passes);
+    // S is orthonormal to FP32 rounding only; correct H to first order in
+    // S^T S - I, with the Gram of the basis the X pass actually used.
+    if (tc(use32))
+        gram64(s_, nullptr, ws_.Wb, ws_.Wb + (size_t)PP * mat_->dpad, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr);
+    else
+        gram64(s_, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr);
+    ortho_correct(s_, ws_.H, ws_.Gm, p, ws_.Hc);
+    sym_eig(s_, ws_.Hc, p, ws_.evals, ws_.evecs, ws_.eigwork, passes);
 }
 
 void Engine::normalize(float *z) {
@@ -560,9 +569,16 @@ static double ms_since(std::chrono::steady_clock::time_point t0) {
 static bool outer_stop(const std::vector<double> &E, double eps, int ell, int min_outer) {
     if (ell + 1 < std::max(3, min_outer)) return false;
     const size_t n = E.size();
+    const size_t w = std::min<size_t>(4, n - 2);
     const double d1 = E[n - 2] - E[n - 1];
-    const double d0 = E[n - 3] - E[n - 2];
-    double r = d0 > 0 ? d1 / d0 : 0.99;
+    const double d0 = E[n - 2 - w] - E[n - 1 - w];
+    double r;
+    if (d0 > 0 && d1 > 0)
+        r = std::pow(d1 / d0, 1.0 / (double)w);
+    else if (d0 > 0)
+        r = 0.0;
+    else
+        r = 0.99;
     r = std::min(std::max(r, 0.0), 0.99);
     const double remaining = std::max(d1, 0.0) * r / (1.0 - r);
     return remaining <= 0.25 * eps * E[n - 1];

@@ -117,7 +117,7 @@ struct Workspace {
     float *S = nullptr, *W = nullptr, *Wt = nullptr, *M = nullptr, *T1 = nullptr, *U = nullptr;
     float *Wr = nullptr, *Q = nullptr, *Y = nullptr, *Gp = nullptr;
     int nchunks = 0;
-    double *H = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
+    double *H = nullptr, *Hc = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;
     __nv_bfloat16 *Wb = nullptr, *Yb = nullptr;  // BF16 hi/lo operands of the tensor-core passes

@@ -4,6 +4,7 @@
 // eigenproblem of Algorithm 2 (cyclic Jacobi in one CTA, Rayleigh quotients in
 // FP64), and small vector helpers.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -13,15 +14,22 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Gram G = A^T A.  Each CTA takes row tiles of 64 rows; thread owns 4x4 blocks
-// of (a, b) pairs with a-block <= b-block; FP32 products summed over a tile,
-// then added to FP64 accumulators; partials reduced in fixed order.
+// of (a, b) pairs with a-block <= b-block; partials reduced in fixed order.
+// kF64 = false: FP32 products summed over a tile, then added to FP64
+// accumulators (tall n x p blocks).  kF64 = true: every product accumulated in
+// FP64 (d x p bases, whose Gram must resolve deviations from I near FP32
+// rounding).  With Ah != nullptr, A is read as the BF16 pair Ah + Al
+// (column-major, leading dimension rows), a sum that FP32 holds exactly.
 // ---------------------------------------------------------------------------
 constexpr int kGR = 64;        // rows per tile
 constexpr int kGMaxBlk = 2;    // 4x4 blocks per thread (406 blocks at p = 112 -> 2 per thread)
 
-__global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, int64_t rows,
+template <bool kF64>
+__global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, const __nv_bfloat16 *__restrict__ Ah,
+                                                   const __nv_bfloat16 *__restrict__ Al, int64_t rows,
                                                    int64_t rs, int64_t cs, int p, int p4,
                                                    double *__restrict__ part) {
+    using T = typename std::conditional<kF64, double, float>::type;
     extern __shared__ __align__(16) float As[];  // [kGR][p4]
     const int tid = threadIdx.x;
     const int nb = p4 / 4;
@@ -62,29 +70,34 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
                 r = e / p4;
             }
             const int64_t row = t0 + r;
-            As[r * p4 + j] = (row < rows && j < p) ? A[row * rs + (int64_t)j * cs] : 0.0f;
+            float v = 0.0f;
+            if (row < rows && j < p) {
+                const int64_t o = row * rs + (int64_t)j * cs;
+                v = Ah ? __bfloat162float(Ah[o]) + __bfloat162float(Al[o]) : A[o];
+            }
+            As[r * p4 + j] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kGMaxBlk; ++u) {
             if (u < nown) {
-                float f[16];
+                T f[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) f[e] = 0.0f;
+                for (int e = 0; e < 16; ++e) f[e] = kF64 ? acc[u][e] : 0.0f;
                 const float *pa = As + 4 * ba[u];
                 const float *pb = As + 4 * bb[u];
                 for (int r = 0; r < kGR; ++r) {
                     const float4 x = *reinterpret_cast<const float4 *>(pa + r * p4);
                     const float4 y = *reinterpret_cast<const float4 *>(pb + r * p4);
-                    const float xa[4] = {x.x, x.y, x.z, x.w};
-                    const float ya[4] = {y.x, y.y, y.z, y.w};
+                    const T xa[4] = {x.x, x.y, x.z, x.w};
+                    const T ya[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) f[4 * i + j] = fmaf(xa[i], ya[j], f[4 * i + j]);
+                        for (int j = 0; j < 4; ++j) f[4 * i + j] = fma(xa[i], ya[j], f[4 * i + j]);
                 }
 #pragma unroll
-                for (int e = 0; e < 16; ++e) acc[u][e] += (double)f[e];
+                for (int e = 0; e < 16; ++e) acc[u][e] = kF64 ? (double)f[e] : acc[u][e] + (double)f[e];
             }
         }
     }
@@ -122,6 +135,29 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, 
     }
     for (; c < nparts; ++c) s0 += part[c * stride + off];
     G[e] = (s0 + s1) + (s2 + s3);
+}
+
+// Rayleigh-Ritz on a basis S that is orthonormal only to rounding: with
+// G = S^T S = I + F and H = S^T A S, the Ritz values of the orthonormalised
+// basis S G^(-1/2) are those of G^(-1/2) H G^(-1/2) = H - (F H + H F)/2 + O(F^2)
+// = 2H - (G H + H G)/2 + O(F^2).  One CTA per column j, thread = row i; G and
+// H symmetric and column-major.
+__global__ void ortho_correct_kernel(const double *__restrict__ H, const double *__restrict__ G, int p,
+                                     double *__restrict__ Hc) {
+    __shared__ double hj[LRA_MAX_P], gj[LRA_MAX_P];
+    const int j = blockIdx.x, i = threadIdx.x;
+    if (i < p) {
+        hj[i] = H[i + (int64_t)j * p];
+        gj[i] = G[i + (int64_t)j * p];
+    }
+    __syncthreads();
+    if (i >= p) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int l = 0; l < p; ++l) {
+        a0 = fma(G[i + (int64_t)l * p], hj[l], a0);  // (G H)_ij, G_il = G_li
+        a1 = fma(H[i + (int64_t)l * p], gj[l], a1);  // (H G)_ij
+    }
+    Hc[i + (int64_t)j * p] = 2.0 * hj[i] - 0.5 * (a0 + a1);
 }
 
 int gram_blocks(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, kGR), 152)); }
@@ -588,9 +624,26 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
     const int nb = gram_blocks(rows);
     const size_t smem = sizeof(float) * kGR * p4;
     LRA_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double) * nb * p4 * p4, s));
-    gram_kernel<<<nb, 256, smem, s>>>(A, rows, rs, cs, p, p4, scratch);
+    gram_kernel<false><<<nb, 256, smem, s>>>(A, nullptr, nullptr, rows, rs, cs, p, p4, scratch);
     LRA_LAUNCHED();
     gram_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
+    LRA_LAUNCHED();
+}
+
+void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, int64_t rows,
+            int64_t ld, int p, double *G, double *scratch) {
+    const int p4 = (int)round_up(p, 4);
+    const int nb = gram_blocks(rows);
+    const size_t smem = sizeof(float) * kGR * p4;
+    LRA_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double) * nb * p4 * p4, s));
+    gram_kernel<true><<<nb, 256, smem, s>>>(A, Ah, Al, rows, 1, ld, p, p4, scratch);
+    LRA_LAUNCHED();
+    gram_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
+    LRA_LAUNCHED();
+}
+
+void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc) {
+    ortho_correct_kernel<<<p, (unsigned)round_up(p, 32), 0, s>>>(H, G, p, Hc);
     LRA_LAUNCHED();
 }
 

@@ -79,6 +79,14 @@ void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_
 int64_t gram_scratch(int p);
 void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, int p, double *G,
           double *scratch);
+// G = A^T A with every product accumulated in FP64; A column-major rows x p
+// (leading dimension ld), read as FP32 A or, when Ah != nullptr, as the BF16
+// pair Ah + Al.  scratch >= gram_scratch(p) doubles
+void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, int64_t rows,
+            int64_t ld, int p, double *G, double *scratch);
+// Hc = 2H - (G H + H G)/2: Rayleigh-Ritz matrix of the orthonormalised basis
+// to first order in G - I (all p x p FP64 column-major, symmetric)
+void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc);
 // Cholesky G = R^T R (upper R), Rinv = R^-1 as FP32 p x p row-major;
 // status[0] = 0 ok / 1 not positive definite
 void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status);
