@@ -311,6 +311,16 @@ def run_lra(args):
         roof = {"bound": "latency", "achieved": None, "peak": None, "unit": "steps/s",
                 "frac": None, "traffic": None, "kernel": "svrg_inner_kernel"}
 
+    # every timed kernel class: launches, time, X-pass GB/s (algorithmic bytes)
+    per_kernel = {}
+    for kk in ("xtw", "xy", "inner"):
+        if cnt[kk] > 0:
+            e = {"launches": cnt[kk], "ms_total": tot[kk], "ms_per_launch": tot[kk] / cnt[kk]}
+            if kk in cols:
+                pav = cols[kk] / cnt[kk]
+                e["x_pass_gbs"] = (wl.d * wl.n * esize + (wl.d + wl.n) * pav * 4) / (tot[kk] / cnt[kk] / 1e3) / 1e9
+            per_kernel[kk] = e
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -368,6 +378,7 @@ def run_lra(args):
             "e2e": e2e,
             "gpu_launches": int(sum(r.kernel_launches for _, r in reps)),
             "kernel_ms": {k: v / args.steps for k, v in tot.items()},
+            "kernels": per_kernel,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -281,4 +281,6 @@ WORKLOADS = {
     "steep_head_4096x65536": Workload("steep_head_4096x65536", 4096, 65536, 20, 40, 4096, 2, "f32"),
     # BF16 (and FP32) dense, d=8192, n=1048576, k=50, p=100
     "exp_two_gaps_8192x1048576": Workload("exp_two_gaps_8192x1048576", 8192, 1048576, 50, 100, 640, 3, "bf16"),
+    # the same spectrum and d with n = 65536 (X = 1.07 GB BF16): profiling captures
+    "exp_two_gaps_8192x65536": Workload("exp_two_gaps_8192x65536", 8192, 65536, 50, 100, 640, 3, "bf16"),
 }

@@ -145,10 +145,29 @@ def gaussian_block(seed: int, stream: int, a: int, d: int, p: int) -> np.ndarray
 # Setup: column norms and the sampling distribution q_i (a reading of Thm. 3)
 # ----------------------------------------------------------------------------
 
-def colnorms(Xt: np.ndarray) -> tuple[np.ndarray, float]:
+def is_sparse(Xt) -> bool:
+    """True for a scipy.sparse X^T (row i = column x_i of X)."""
+    try:
+        import scipy.sparse as sp
+    except ImportError:  # pragma: no cover
+        return False
+    return sp.issparse(Xt)
+
+
+def as64(Xt):
+    """X^T with its stored values widened exactly to FP64 (dense or CSR)."""
+    if is_sparse(Xt):
+        return Xt.tocsr().astype(np.float64, copy=False)
+    return np.asarray(Xt, dtype=np.float64)
+
+
+def colnorms(Xt) -> tuple[np.ndarray, float]:
     """||x_i||^2 for every column of X and ||X||_F^2, in FP64 (Xt is (n, d))."""
-    X64 = np.asarray(Xt, dtype=np.float64)
-    norm2 = np.einsum("ij,ij->i", X64, X64)
+    X64 = as64(Xt)
+    if is_sparse(X64):
+        norm2 = np.asarray(X64.multiply(X64).sum(axis=1)).ravel()
+    else:
+        norm2 = np.einsum("ij,ij->i", X64, X64)
     return norm2, float(np.sum(norm2))
 
 
@@ -207,10 +226,10 @@ def sample_indices(table: SamplingTable, key: int, m: int) -> np.ndarray:
 # The anchor pass and the inner loop (SVRGsolve)
 # ----------------------------------------------------------------------------
 
-def x_apply(Xt: np.ndarray, W: np.ndarray) -> np.ndarray:
+def x_apply(Xt, W: np.ndarray) -> np.ndarray:
     """A W = X (X^T W) with X read as stored, in FP64 (Xt is (n, d))."""
-    X64 = np.asarray(Xt, dtype=np.float64)
-    return X64.T @ (X64 @ W)
+    X64 = as64(Xt)
+    return np.asarray(X64.T @ np.asarray(X64 @ W))
 
 
 def anchor(Xt: np.ndarray, Wt: np.ndarray, B: np.ndarray, lam: float) -> np.ndarray:
@@ -238,6 +257,9 @@ def _clib():
         fn = getattr(lib, name)
         fn.argtypes = [i64, i64, vp, i64, vp, i64, vp, dbl, dbl, vp, vp, vp]
         fn.restype = None
+    fn = lib.oracle_svrg_inner_csc
+    fn.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, vp, vp, vp]
+    fn.restype = None
     _CLIB = lib
     return lib
 
@@ -266,6 +288,16 @@ def svrg_epoch(Xt: np.ndarray, W: np.ndarray, Wt: np.ndarray, M: np.ndarray,
     Mc = np.asfortranarray(M, dtype=np.float64)
     idx64 = np.ascontiguousarray(idx, dtype=np.int64)
     c64 = np.ascontiguousarray(c, dtype=np.float64)
+    if is_sparse(Xt):
+        # rows of X^T = columns of X, in compressed form (factored update, C7b reading)
+        Xr = Xt.tocsr()
+        colptr = np.ascontiguousarray(Xr.indptr, dtype=np.int64)
+        rowidx = np.ascontiguousarray(Xr.indices, dtype=np.int32)
+        val = np.ascontiguousarray(Xr.data, dtype=np.float32)
+        lib.oracle_svrg_inner_csc(d, p, colptr.ctypes.data, rowidx.ctypes.data, val.ctypes.data,
+                                  idx64.ctypes.data, idx64.shape[0], c64.ctypes.data, float(eta),
+                                  float(lam), Wtc.ctypes.data, Mc.ctypes.data, Wc.ctypes.data)
+        return np.array(Wc)
     Xc = np.ascontiguousarray(Xt)
     if Xc.dtype == np.float64:
         fn = lib.oracle_svrg_inner_f64
@@ -409,7 +441,7 @@ def rayleigh_ritz(Xt: np.ndarray, S: np.ndarray):
     """Algorithm 2 with C = X X^T: eigendecomposition of S^T C S = (X^T S)^T (X^T S).
 
     Returns (rho descending, U_hat, Q = X^T S, H)."""
-    Q = np.asarray(Xt, dtype=np.float64) @ S
+    Q = np.asarray(as64(Xt) @ S)
     H = Q.T @ Q
     rho, Uh = sym_eig_desc(H)
     return rho, Uh, Q, H
@@ -431,7 +463,7 @@ def lambda1_estimate(ctx: Context, eps: float = 0.25) -> float:
         y = x_apply(ctx.Xt, z)
         ctx.x_passes += 2
         z = y / np.linalg.norm(y)
-    q = np.asarray(ctx.Xt, dtype=np.float64) @ z
+    q = np.asarray(as64(ctx.Xt) @ z)
     ctx.x_passes += 1
     return float(np.sum(q * q))
 
@@ -638,9 +670,9 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
 
 def frobenius_error(Xt: np.ndarray, U: np.ndarray) -> float:
     """||X - U U^T X||_F^2 = ||X||_F^2 - ||U^T X||_F^2 for orthonormal U."""
-    X64 = np.asarray(Xt, dtype=np.float64)
-    fro2 = float(np.sum(X64 * X64))
-    P = X64 @ U
+    X64 = as64(Xt)
+    fro2 = colnorms(X64)[1]
+    P = np.asarray(X64 @ U)
     return fro2 - float(np.sum(P * P))
 
 

@@ -67,3 +67,54 @@ void oracle_svrg_inner_f32(int64_t d, int64_t p, const float *X, int64_t ldx,
 {
     inner_loop(d, p, NULL, X, ldx, idx, m, c, eta, lam, Wt, M, W);
 }
+
+/*
+ * The same epoch for a sparse X given by its columns x_i in compressed form
+ * (colptr[n+1], rowidx[nnz], val[nnz] FP32: column i holds val[k] at row
+ * rowidx[k] for colptr[i] <= k < colptr[i+1]).
+ *
+ * A step touches only the rows of x_i once W - Wt is kept in the factored form
+ *     W - Wt = a Z + b M,
+ * which the dense step maps to itself (with g = 1 - eta lambda):
+ *     W' - Wt = g (a Z + b M) + eta c_i x_i r - eta M
+ *             = a' (Z + (eta c_i / a') x_i r) + b' M,   a' = g a,  b' = g b - eta,
+ * and r = x_i^T (W - Wt) = a (x_i^T Z) + b (x_i^T M).  Start: Z = W - Wt, a = 1,
+ * b = 0.  When a falls below 2^-30 the factor is folded into Z (Z <- a Z,
+ * a <- 1).  End: W = Wt + a Z + b M.
+ */
+void oracle_svrg_inner_csc(int64_t d, int64_t p, const int64_t *colptr, const int32_t *rowidx,
+                           const float *val, const int64_t *idx, int64_t m, const double *c,
+                           double eta, double lam, const double *Wt, const double *M, double *W)
+{
+    double *Z = (double *)malloc(sizeof(double) * (size_t)(d * p > 0 ? d * p : 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)(p > 0 ? p : 1));
+    const double g = 1.0 - eta * lam;
+    double a = 1.0, b = 0.0;
+    for (int64_t e = 0; e < d * p; ++e) Z[e] = W[e] - Wt[e];
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t i = idx[t];
+        const int64_t k0 = colptr[i], k1 = colptr[i + 1];
+        for (int64_t j = 0; j < p; ++j) {
+            double sz = 0.0, sm = 0.0;
+            for (int64_t k = k0; k < k1; ++k) {
+                const int64_t row = rowidx[k];
+                sz += (double)val[k] * Z[j * d + row];
+                sm += (double)val[k] * M[j * d + row];
+            }
+            r[j] = a * sz + b * sm;
+        }
+        const double a1 = g * a;
+        b = g * b - eta;
+        const double s = eta * c[i] / a1;
+        for (int64_t j = 0; j < p; ++j)
+            for (int64_t k = k0; k < k1; ++k) Z[j * d + rowidx[k]] += s * (double)val[k] * r[j];
+        a = a1;
+        if (a < 0x1p-30) {
+            for (int64_t e = 0; e < d * p; ++e) Z[e] *= a;
+            a = 1.0;
+        }
+    }
+    for (int64_t e = 0; e < d * p; ++e) W[e] = Wt[e] + a * Z[e] + b * M[e];
+    free(Z);
+    free(r);
+}
