@@ -122,9 +122,30 @@ class ClockSampler:
 # the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def theory_rate(wl, lam):
+def sparse_reference(name):
+    """fro2, opt, lambda_k, lambda_{p+1} of a seeded sparse workload, as written
+    by tests/golden/make_sparse_opt.py (oracle only)."""
+    path = os.path.join(ROOT, "tests", "golden", "zipf_csr_opt.txt")
+    with open(path) as f:
+        for line in f:
+            if line.startswith(name + " "):
+                kv = dict(t.split("=") for t in line.split()[1:])
+                return {k: float(v) for k, v in kv.items()}
+    raise KeyError(f"no reference optimum for {name} in {path}")
+
+
+def spectrum(wl):
+    """(opt, lambda_k, lambda_{p+1}) of a workload: closed form for the planted
+    spectra, the stored reference for the sparse ones."""
+    if wl.storage == "csr":
+        ref = sparse_reference(wl.name)
+        return ref["opt"], ref["lambda_k"], ref["lambda_p1"]
     s = wl.sigma()
-    lk, lp1 = s[wl.k - 1] ** 2, s[wl.p] ** 2
+    return wl.opt(), s[wl.k - 1] ** 2, s[wl.p] ** 2
+
+
+def theory_rate(wl, lam):
+    _, lk, lp1 = spectrum(wl)
     return ((lam - lk) / (lam - lp1)) ** 2
 
 
@@ -134,16 +155,16 @@ def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
     seconds per outer iteration, the oracle's shift, its E trace)."""
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     from oracle import lra_oracle as O
-    X64 = np.asarray(Xt_host, dtype=np.float64)
+    X64 = O.as64(Xt_host)
     pol = O.SHIFT_FAR if args.shift == "far" else O.SHIFT_PAPER
-    s = wl.sigma()
-    delta = (s[wl.k - 1] ** 2 - s[wl.p] ** 2) / 1.5
+    _, lk, lp1 = spectrum(wl)
+    delta = (lk - lp1) / 1.5
     t0 = time.perf_counter()
     ctx = O.Context(X64, args.seed, O.Options())
     lh = O.lambda1_estimate(ctx)
     t_fixed = time.perf_counter() - t0
     o = O.Options(shift_policy=pol, delta=delta, min_outer=outer_sample, max_outer=outer_sample,
-                  tau=1e-5 if args.storage == "f32" else 1e-3)
+                  tau=1e-3 if args.storage == "bf16" else 1e-5)
     t0 = time.perf_counter()
     r = O.solve(X64, wl.k, wl.p, args.eps, args.seed, o, lam1_hat=lh)
     t_outer = time.perf_counter() - t0
@@ -153,7 +174,7 @@ def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
 def predicted_outer(wl, lam, E_trace, eps):
     """Outer iterations at which the stop rule fires, from the sampled Ritz
     error and the asymptotic rate ((lambda - lambda_k)/(lambda - lambda_{p+1}))^2."""
-    opt = wl.opt()
+    opt = spectrum(wl)[0]
     r = theory_rate(wl, lam)
     excess = max(E_trace[-1] - opt, 1e-300)
     target = 0.25 * eps * opt
@@ -173,15 +194,141 @@ def make_workload(args, device):
     return wl, Xt
 
 
+class DenseSource:
+    """A planted-spectrum dense X (FP32 on the device) and its accounting."""
+
+    tensor = True
+
+    def __init__(self, args, wl, device, lra):
+        import torch
+        self.wl, self.lra, self.args = wl, lra, args
+        self.storage = lra.LRA_F32 if args.storage == "f32" else lra.LRA_BF16
+        self.esize = 4 if args.storage == "f32" else 2
+        self.Xt, _ = L.planted_torch(wl.d, wl.n, wl.sigma(), wl.seed, device=device)
+        torch.cuda.synchronize()
+        self.x_bytes = wl.d * wl.n * self.esize
+        self.h2d_bytes = wl.d * wl.n * 4
+        self.Xh = None
+
+    def create(self, ctx):
+        return self.lra.lra_create_dense(ctx, self.wl.d, self.wl.n, self.lra.LRA_F32, self.Xt, self.wl.d, True,
+                                         self.storage)
+
+    def to_host(self):
+        import torch
+        if self.Xh is None:
+            self.Xh = torch.empty(self.Xt.shape, dtype=torch.float32, pin_memory=True)
+            self.Xh.copy_(self.Xt)
+        return self.Xh
+
+    def drop_device(self):
+        self.to_host()
+        del self.Xt
+        self.Xt = None
+
+    def create_from_host(self, ctx):
+        return self.lra.lra_create_dense(ctx, self.wl.d, self.wl.n, self.lra.LRA_F32, self.Xh, self.wl.d, False,
+                                         self.storage)
+
+    def err(self, U):
+        import torch
+        X = self.Xt if self.Xt is not None else self.Xh.to(U.device)
+        Xd = X.double()
+        P = Xd @ U.double().T
+        e = float((Xd * Xd).sum()) - float((P * P).sum())
+        del Xd, P
+        torch.cuda.empty_cache()
+        return e
+
+    def pass_bytes(self, kind, pav):
+        return self.x_bytes + (self.wl.d + self.wl.n) * pav * 4
+
+    def oracle_input(self):
+        return self.to_host().numpy()
+
+
+class CsrSource:
+    """A seeded Zipf CSR X: host arrays, device copies, and its accounting."""
+
+    tensor = False
+
+    def __init__(self, args, wl, device, lra):
+        import torch
+        self.wl, self.lra, self.args = wl, lra, args
+        self.storage = lra.LRA_F32
+        self.esize = 4
+        self.rowptr, self.colidx, self.val = wl.csr()
+        self.nnz = int(self.rowptr[-1])
+        self.dev = [torch.from_numpy(a).to(device) for a in (self.rowptr, self.colidx, self.val)]
+        self.pinned = None
+        self.x_bytes = self.nnz * 8
+        self.h2d_bytes = self.rowptr.nbytes + self.colidx.nbytes + self.val.nbytes
+        self._sp = None
+
+    def create(self, ctx):
+        wl = self.wl
+        return self.lra.lra_create_csr(ctx, wl.d, wl.n, self.nnz, *self.dev, True)
+
+    def to_host(self):
+        import torch
+        if self.pinned is None:
+            self.pinned = []
+            for a in (self.rowptr, self.colidx, self.val):
+                t = torch.empty(a.shape, dtype={np.dtype(np.int64): torch.int64, np.dtype(np.int32): torch.int32,
+                                                np.dtype(np.float32): torch.float32}[a.dtype], pin_memory=True)
+                t.copy_(torch.from_numpy(a))
+                self.pinned.append(t)
+        return self.pinned
+
+    def drop_device(self):
+        self.to_host()
+        self.dev = None
+
+    def create_from_host(self, ctx):
+        wl = self.wl
+        return self.lra.lra_create_csr(ctx, wl.d, wl.n, self.nnz, *self.pinned, False)
+
+    def xt(self):
+        if self._sp is None:
+            import scipy.sparse as sp
+            self._sp = sp.csr_matrix((self.val, self.colidx, self.rowptr), shape=(self.wl.d, self.wl.n)).T.tocsr()
+        return self._sp
+
+    def err(self, U):
+        import scipy.sparse  # noqa: F401
+        Xt = self.xt()
+        Uh = U.double().cpu().numpy().T                       # d x k
+        P = np.asarray(Xt.astype(np.float64) @ Uh)
+        v = self.val.astype(np.float64)
+        return float(np.sum(v * v)) - float(np.sum(P * P))
+
+    def pass_bytes(self, kind, pav):
+        wl = self.wl
+        # compressed index + value of every non-zero, the line pointers, the
+        # dense operand and the result (gathers of the operand hit L2)
+        if kind == "xtw":
+            return self.nnz * 8 + (wl.n + 1) * 8 + (wl.d + wl.n) * pav * 4
+        return self.nnz * 8 + (wl.d + 1) * 8 + (wl.n + wl.d) * pav * 4
+
+    def oracle_input(self):
+        return self.xt()
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     import torch
-    wl, Xt = make_workload(args, f"cuda:{local}")
-    Xh = Xt.cpu().numpy()
-    del Xt
-    torch.cuda.empty_cache()
+    wl = L.WORKLOADS[args.workload]
+    if wl.storage == "csr":
+        import scipy.sparse as sp
+        rowptr, colidx, val = wl.csr()
+        Xh = sp.csr_matrix((val, colidx, rowptr), shape=(wl.d, wl.n)).T.tocsr()
+    else:
+        wl, Xt = make_workload(args, f"cuda:{local}")
+        Xh = Xt.cpu().numpy()
+        del Xt
+        torch.cuda.empty_cache()
     threads = len(os.sched_getaffinity(0))
     lam1 = None
     vals = []
@@ -202,7 +349,8 @@ def run_reference(args):
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
-                   "storage": args.storage, "shift": args.shift, "eps": args.eps},
+                   "storage": "csr" if wl.storage == "csr" else args.storage, "shift": args.shift,
+                   "eps": args.eps},
         "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -221,16 +369,16 @@ def run_lra(args):
     device = f"cuda:{local}"
     import paper_1607_02925_gb300 as lra
 
-    wl, Xt = make_workload(args, device)
-    storage = lra.LRA_F32 if args.storage == "f32" else lra.LRA_BF16
-    esize = 4 if args.storage == "f32" else 2
-    s = wl.sigma()
-    delta = (s[wl.k - 1] ** 2 - s[wl.p] ** 2) / 1.5
+    wl = L.WORKLOADS[args.workload]
+    src = (CsrSource if wl.storage == "csr" else DenseSource)(args, wl, device, lra)
+    storage_name = "csr" if wl.storage == "csr" else args.storage
+    opt_val, lk, lp1 = spectrum(wl)
+    delta = (lk - lp1) / 1.5
     pol = lra.LRA_SHIFT_FAR if args.shift == "far" else lra.LRA_SHIFT_PAPER
     opt = lra.options(shift_policy=pol, delta=delta, profile=1)
 
     ctx = lra.lra_init(local)
-    mat = lra.lra_create_dense(ctx, wl.d, wl.n, lra.LRA_F32, Xt, wl.d, True, storage)
+    mat = src.create(ctx)
     stream = torch.cuda.ExternalStream(lra.lra_ctx_stream(ctx), device=device)
     U = torch.zeros(wl.k, wl.d, dtype=torch.float32, device=device)
     ritz = torch.zeros(wl.k, dtype=torch.float64, device=device)
@@ -265,14 +413,9 @@ def run_lra(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
 
-    # accuracy of the last solve, off the clock (FP64, closed-form optimum)
-    Xd = Xt.double()
-    P = Xd @ U.double().T
-    fro2 = float((Xd * Xd).sum())
-    err = fro2 - float((P * P).sum())
-    ratio = err / wl.opt()
-    del Xd, P
-    torch.cuda.empty_cache()
+    # accuracy of the last solve, off the clock (FP64 error against the
+    # closed-form or stored reference optimum)
+    ratio = src.err(U) / opt_val
 
     # roofline of the dominant kernel from its live CUDA-event timing
     peaks, peak_kind = measured_peaks()
@@ -284,32 +427,37 @@ def run_lra(args):
     cols = {"xtw": sum(r.xtw_cols for _, r in reps), "xy": sum(r.xy_cols for _, r in reps)}
     dom = max(tot, key=lambda k: tot[k])
     roof = None
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     if dom in ("xtw", "xy") and cnt[dom] > 0:
         pav = cols[dom] / cnt[dom]
-        bytes_l = wl.d * wl.n * esize + (wl.d + wl.n) * pav * 4
-        flops_l = 2.0 * wl.d * wl.n * pav
+        bytes_l = src.pass_bytes(dom, pav)
         t_l = tot[dom] / cnt[dom] / 1e3
         hbm = peaks["hbm_gbs"] * 1e9
-        # both storages run the X passes on tensor cores: BF16 X with 2 BF16 MMAs
-        # per k-step (hi/lo small operand), FP32 X as a BF16 pair with 3; the
-        # executed tensor flops are compared with the measured sustained BF16 peak
-        tensor = True
-        mmas = 2 if args.storage == "bf16" else 3
-        alu = peaks["bf16_tflops_sustained"] * 1e12 / mmas
-        if bytes_l / hbm >= flops_l / alu:
+        if src.tensor:
+            # dense X passes run on tensor cores: BF16 X with 2 BF16 MMAs per
+            # k-step (hi/lo small operand), FP32 X as a BF16 pair with 3; the
+            # executed tensor flops are compared with the measured sustained BF16 peak
+            flops_l = 2.0 * wl.d * wl.n * pav
+            mmas = 2 if args.storage == "bf16" else 3
+            tens = peaks["bf16_tflops_sustained"] * 1e12 / mmas
+            compute_bound = bytes_l / hbm < flops_l / tens
+        else:
+            compute_bound = False
+        if compute_bound:
+            roof = {"bound": "tensor", "achieved": flops_l / t_l / 1e12, "peak": tens / 1e12,
+                    "unit": "TFLOP/s", "frac": flops_l / t_l / tens, "traffic": None}
+        else:
             roof = {"bound": "hbm", "achieved": bytes_l / t_l / 1e9, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": bytes_l / t_l / hbm, "traffic": None}
-        else:
-            roof = {"bound": "tensor" if tensor else "alu", "achieved": flops_l / t_l / 1e12, "peak": alu / 1e12,
-                    "unit": "TFLOP/s", "frac": flops_l / t_l / alu, "traffic": None}
-        roof.update({"kernel": ("xtw" if dom == "xtw" else "xy") + ("_tc_kernel" if tensor else "_kernel"),
+        names = {("xtw", True): "xtw_tc_kernel", ("xy", True): "xy_tc_kernel",
+                 ("xtw", False): "spmm_xt_kernel", ("xy", False): "spmm_x_kernel"}
+        roof.update({"kernel": names[(dom, src.tensor)],
                      "launches": cnt[dom], "ms_per_launch": t_l * 1e3,
                      "algorithmic_bytes_per_launch": bytes_l,
                      "x_pass_gbs": bytes_l / t_l / 1e9, "peak_source": peak_kind})
     elif cnt["inner"] > 0:
         roof = {"bound": "latency", "achieved": None, "peak": None, "unit": "steps/s",
-                "frac": None, "traffic": None, "kernel": "svrg_inner_kernel"}
+                "frac": None, "traffic": None,
+                "kernel": "inner_csc_kernel" if wl.storage == "csr" else "svrg_inner_kernel"}
 
     # every timed kernel class: launches, time, X-pass GB/s (algorithmic bytes)
     per_kernel = {}
@@ -318,40 +466,35 @@ def run_lra(args):
             e = {"launches": cnt[kk], "ms_total": tot[kk], "ms_per_launch": tot[kk] / cnt[kk]}
             if kk in cols:
                 pav = cols[kk] / cnt[kk]
-                e["x_pass_gbs"] = (wl.d * wl.n * esize + (wl.d + wl.n) * pav * 4) / (tot[kk] / cnt[kk] / 1e3) / 1e9
+                e["x_pass_gbs"] = src.pass_bytes(kk, pav) / (tot[kk] / cnt[kk] / 1e3) / 1e9
             per_kernel[kk] = e
 
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        Xh = torch.empty(Xt.shape, dtype=torch.float32, pin_memory=True)
-        Xh.copy_(Xt)
         Uh = torch.empty(wl.k, wl.d, dtype=torch.float32, pin_memory=True)
         rh = torch.empty(wl.k, dtype=torch.float64, pin_memory=True)
         lra.lra_mat_destroy(mat)
         mat = None
-        del Xt
+        src.drop_device()
         torch.cuda.empty_cache()
         times = []
         for _ in range(args.steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            m2 = lra.lra_create_dense(ctx, wl.d, wl.n, lra.LRA_F32, Xh, wl.d, False, storage)
+            m2 = src.create_from_host(ctx)
             lra.lra_solve(m2, wl.k, wl.p, args.eps, args.seed, opt, Uh, rh, lra.LraReport())
             lra.lra_mat_destroy(m2)
             times.append(time.perf_counter() - t0)
         e2e = {"value": statistics.mean(times[1:]), "unit": "s",
-               "h2d_bytes_per_step": wl.d * wl.n * 4,
+               "h2d_bytes_per_step": src.h2d_bytes,
                "d2h_bytes_per_step": wl.d * wl.k * 4 + wl.k * 8}
-    else:
-        Xh = None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
-        if Xh is None:
-            Xh = Xt.cpu()
-        t_fixed, t_outer, lam, E = oracle_sample(wl, Xh.numpy(), args, None, args.cpu_sample_outer, threads)
+        t_fixed, t_outer, lam, E = oracle_sample(wl, src.oracle_input(), args, None, args.cpu_sample_outer,
+                                                 threads)
         Lg = last.outer_iters
         cpu = {"value": t_fixed + t_outer * Lg, "unit": "s", "cores": threads, "kind": "oracle",
                "sample": (f"FP64 oracle on the same X and seeds: lambda_1 estimate ({t_fixed:.1f} s) "
@@ -366,10 +509,10 @@ def run_lra(args):
             "metric": "time-to-eps", "value": ms_step / 1e3, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.storage, "data": "synthetic",
+            "dtype": "f32" if storage_name == "csr" else args.storage, "data": "synthetic",
             "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
-                       "storage": args.storage, "shift": args.shift, "eps": args.eps,
-                       "l2": "inputs larger than L2 (X %.2f GB per pass)" % (wl.d * wl.n * esize / 1e9),
+                       "storage": storage_name, "shift": args.shift, "eps": args.eps,
+                       "l2": "inputs larger than L2 (X %.2f GB per pass)" % (src.x_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"ratio_err_over_opt": ratio, "outer_iters": last.outer_iters,
                          "status": reps[-1][0]},

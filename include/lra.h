@@ -149,9 +149,16 @@ lra_status lra_finalize(lra_ctx *ctx);
 lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, const void *X,
                             int64_t ld, int src_on_device, lra_dtype storage, lra_mat **out);
 
-/* Copy a sparse X given as CSR of its d rows (rowptr[d+1] int64, colidx[nnz]
- * int32 in [0, n), val[nnz] float).  Currently returns LRA_EUNSUPPORTED after
- * validating its arguments. */
+/* Copy a sparse X (d x n, FP32 values) given as CSR of its d rows from host
+ * or device memory (src_on_device = 0/1): rowptr[d+1] int64 with rowptr[0] = 0
+ * and rowptr[d] = nnz, colidx[nnz] int32 in [0, n) strictly increasing within
+ * each row (no duplicates), val[nnz] finite.  The library keeps its own copy
+ * plus the compressed columns x_i (the sampled columns of the SVRG steps and
+ * the operand of X^T W, Sec. 2.3 whose cost is O(nnz(X)) per anchor), so the
+ * caller may free the arrays on return.  Every solve on a sparse X runs in
+ * FP32 on the CUDA cores (the paper's nnz(X) regime, Theorem 3).  Requires
+ * 1 <= d, 2 <= n, d and n < 2^31; invalid arrays give LRA_EINVAL (no matrix
+ * is created; lra_last_error() names the violated rule). */
 lra_status lra_create_csr(lra_ctx *ctx, int64_t d, int64_t n, int64_t nnz, const int64_t *rowptr,
                           const int32_t *colidx, const float *val, int src_on_device, lra_mat **out);
 

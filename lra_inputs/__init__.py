@@ -266,7 +266,11 @@ class Workload:
             return sigma_steep_head(self.r)
         if self.name.startswith("exp_two_gaps"):
             return sigma_exp_two_gaps(self.r)
-        raise ValueError(self.name)
+        raise ValueError(f"{self.name} has no planted spectrum")
+
+    def csr(self):
+        """(rowptr, colidx, val) of a sparse workload."""
+        return zipf_csr(self.d, self.n, self.seed)
 
     def opt(self) -> float:
         return closed_form_opt(self.sigma(), self.k)
@@ -283,4 +287,8 @@ WORKLOADS = {
     "exp_two_gaps_8192x1048576": Workload("exp_two_gaps_8192x1048576", 8192, 1048576, 50, 100, 640, 3, "bf16"),
     # the same spectrum and d with n = 65536 (X = 1.07 GB BF16): profiling captures
     "exp_two_gaps_8192x65536": Workload("exp_two_gaps_8192x65536", 8192, 65536, 50, 100, 640, 3, "bf16"),
+    # sparse CSR (Zipf term-document), d=50000, n=500000, ~100 non-zeros per column
+    "zipf_csr_50000x500000": Workload("zipf_csr_50000x500000", 50000, 500000, 10, 20, 0, 4, "csr"),
+    # the same law at d=2000, n=20000 (tests and the reference optimum's cross-check)
+    "zipf_csr_2000x20000": Workload("zipf_csr_2000x20000", 2000, 20000, 10, 20, 0, 4, "csr"),
 }

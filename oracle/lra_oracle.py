@@ -665,6 +665,38 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
 
 
 # ----------------------------------------------------------------------------
+# Reference optimum of an X without a planted spectrum
+# ----------------------------------------------------------------------------
+
+def top_eigs_lanczos(Xt, q: int, tol: float = 1e-13) -> np.ndarray:
+    """The q largest eigenvalues of A = X X^T (descending) by ARPACK's implicitly
+    restarted Lanczos on the operator v -> X (X^T v), in FP64 (library routine)."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    X64 = as64(Xt)
+    d = X64.shape[1]
+    op = LinearOperator((d, d), matvec=lambda v: np.asarray(X64.T @ np.asarray(X64 @ v)).ravel(),
+                        dtype=np.float64)
+    w = eigsh(op, k=q, which="LA", tol=tol, return_eigenvectors=False, v0=np.ones(d) / math.sqrt(d))
+    return np.sort(w)[::-1]
+
+
+def plain_subspace_iteration(Xt, k: int, p: int, iters: int, seed: int = 0):
+    """Algorithm 1 on A itself (no shift, exact products): S <- orth(A S) from a
+    Gaussian start, then Algorithm 2; returns the Ritz values rho_1..rho_p."""
+    S = orth(gaussian_block(seed, STREAM_INIT, 0, Xt.shape[1], p))
+    for _ in range(iters):
+        S = orth(x_apply(Xt, S))
+    rho, _, _, _ = rayleigh_ritz(Xt, S)
+    return rho
+
+
+def reference_optimum(Xt, k: int, tol: float = 1e-13) -> float:
+    """opt = ||X - X_k||_F^2 = ||X||_F^2 - sum_{j<=k} lambda_j(X X^T)."""
+    fro2 = colnorms(Xt)[1]
+    return fro2 - float(np.sum(top_eigs_lanczos(Xt, k, tol)[:k]))
+
+
+# ----------------------------------------------------------------------------
 # Metrics (Sec. 1 and Appendix C)
 # ----------------------------------------------------------------------------
 

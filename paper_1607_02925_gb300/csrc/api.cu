@@ -106,7 +106,7 @@ struct Padded {
 };
 
 lra_status check_mat(const lra_mat *m) {
-    if (!m || !m->ctx || !m->X) return einval("null matrix");
+    if (!m || !m->ctx || (!m->X && !m->sp)) return einval("null matrix");
     return LRA_OK;
 }
 
@@ -278,13 +278,111 @@ lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, c
     })
 }
 
+namespace {
+
+// Free every buffer of a sparse matrix record (null entries are skipped).
+void free_sparse(lra_ctx *ctx, lra_mat *m) {
+    auto *sp = m->sp;
+    if (!sp) return;
+    const int64_t d = m->d, n = m->n, dpad = m->dpad, nnz = sp->nnz;
+    if (sp->rowptr) dev_free(ctx, sp->rowptr, sizeof(int64_t) * (d + 1));
+    if (sp->colidx) dev_free(ctx, sp->colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    if (sp->val) dev_free(ctx, sp->val, sizeof(float) * std::max<int64_t>(nnz, 1));
+    if (sp->colptr) dev_free(ctx, sp->colptr, sizeof(int64_t) * (n + 1));
+    if (sp->rowidx) dev_free(ctx, sp->rowidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1));
+    if (sp->cval) dev_free(ctx, sp->cval, sizeof(float) * std::max<int64_t>(nnz, 1));
+    if (sp->item_off) dev_free(ctx, sp->item_off, sizeof(int64_t) * (dpad + 1));
+    if (sp->items) dev_free(ctx, sp->items, sizeof(int2) * std::max<int64_t>(sp->nitems, 1));
+    delete sp;
+    m->sp = nullptr;
+}
+
+}  // namespace
+
 lra_status lra_create_csr(lra_ctx *ctx, int64_t d, int64_t n, int64_t nnz, const int64_t *rowptr,
                           const int32_t *colidx, const float *val, int src_on_device, lra_mat **out) {
-    (void)src_on_device;
     if (!ctx || !out || !rowptr || (nnz > 0 && (!colidx || !val))) return einval("null argument");
     if (d < 1 || n < 2 || nnz < 0) return einval("bad shape");
-    set_error("sparse CSR input is not implemented in this build");
-    return LRA_EUNSUPPORTED;
+    if (n > (int64_t)INT32_MAX || d > (int64_t)INT32_MAX) return einval("d and n must fit in int32");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    lra_mat *m = nullptr;
+    LRA_TRY({
+        DeviceGuard g(ctx->device);
+        m = new lra_mat();
+        m->ctx = ctx;
+        m->d = d;
+        m->n = n;
+        m->dpad = round_up(d, kRowPad);
+        m->storage = LRA_F32;
+        m->sp = new lra_mat::Sparse();
+        auto &sp = *m->sp;
+        sp.nnz = nnz;
+        const cudaStream_t s = ctx->stream;
+        const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const int64_t nz1 = std::max<int64_t>(nnz, 1);
+        int64_t *cnt = nullptr, *scr = nullptr;
+        int *cursor = nullptr, *bad = nullptr;
+        const int64_t scr_len = sparse_scan_scratch(std::max(n, m->dpad));
+        auto free_tmp = [&]() {
+            cudaStreamSynchronize(s);
+            if (cnt) dev_free(ctx, cnt, sizeof(int64_t) * std::max(n, m->dpad));
+            if (scr) dev_free(ctx, scr, sizeof(int64_t) * scr_len);
+            if (cursor) dev_free(ctx, cursor, sizeof(int) * n);
+            if (bad) dev_free(ctx, bad, sizeof(int) * 4);
+            cnt = scr = nullptr;
+            cursor = bad = nullptr;
+        };
+        try {
+            sp.rowptr = static_cast<int64_t *>(dev_alloc(ctx, sizeof(int64_t) * (d + 1)));
+            sp.colidx = static_cast<int32_t *>(dev_alloc(ctx, sizeof(int32_t) * nz1));
+            sp.val = static_cast<float *>(dev_alloc(ctx, sizeof(float) * nz1));
+            LRA_CUDA(cudaMemcpyAsync(sp.rowptr, rowptr, sizeof(int64_t) * (d + 1), kind, s));
+            if (nnz > 0) {
+                LRA_CUDA(cudaMemcpyAsync(sp.colidx, colidx, sizeof(int32_t) * nnz, kind, s));
+                LRA_CUDA(cudaMemcpyAsync(sp.val, val, sizeof(float) * nnz, kind, s));
+            }
+            bad = static_cast<int *>(dev_alloc(ctx, sizeof(int) * 4));
+            csr_check(s, sp.rowptr, sp.colidx, sp.val, d, n, nnz, bad);
+            int hb = 0;
+            LRA_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            LRA_CUDA(cudaStreamSynchronize(s));
+            if (hb) {
+                std::string why = "invalid CSR:";
+                if (hb & 16) why += " rowptr[0] != 0 or rowptr[d] != nnz;";
+                if (hb & 1) why += " row pointers decreasing or out of [0, nnz];";
+                if (hb & 2) why += " column index out of [0, n);";
+                if (hb & 4) why += " column indices not strictly increasing within a row;";
+                if (hb & 8) why += " value not finite;";
+                set_error(why);
+                throw Error{LRA_EINVAL};
+            }
+            // compressed columns (the x_i of the inner loop and of X^T W)
+            sp.colptr = static_cast<int64_t *>(dev_alloc(ctx, sizeof(int64_t) * (n + 1)));
+            sp.rowidx = static_cast<int32_t *>(dev_alloc(ctx, sizeof(int32_t) * nz1));
+            sp.cval = static_cast<float *>(dev_alloc(ctx, sizeof(float) * nz1));
+            cnt = static_cast<int64_t *>(dev_alloc(ctx, sizeof(int64_t) * std::max(n, m->dpad)));
+            scr = static_cast<int64_t *>(dev_alloc(ctx, sizeof(int64_t) * scr_len));
+            cursor = static_cast<int *>(dev_alloc(ctx, sizeof(int) * n));
+            csr_transpose(s, sp.rowptr, sp.colidx, sp.val, d, n, nnz, sp.colptr, sp.rowidx, sp.cval, cnt, cursor,
+                          scr);
+            // row work list of X Y
+            sp.item_off = static_cast<int64_t *>(dev_alloc(ctx, sizeof(int64_t) * (m->dpad + 1)));
+            sparse_row_items(s, sp.rowptr, d, m->dpad, kSparseSeg, cnt, sp.item_off, scr);
+            LRA_CUDA(cudaMemcpyAsync(&sp.nitems, sp.item_off + m->dpad, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            LRA_CUDA(cudaStreamSynchronize(s));
+            sp.items = static_cast<int2 *>(dev_alloc(ctx, sizeof(int2) * std::max<int64_t>(sp.nitems, 1)));
+            sparse_fill_items(s, sp.item_off, m->dpad, sp.items);
+            free_tmp();
+        } catch (...) {
+            free_tmp();
+            free_sparse(ctx, m);
+            delete m;
+            throw;
+        }
+        ctx->nmats.fetch_add(1);
+        *out = m;
+        return LRA_OK;
+    })
 }
 
 lra_status lra_mat_destroy(lra_mat *m) {
@@ -299,6 +397,7 @@ lra_status lra_mat_destroy(lra_mat *m) {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
         const size_t ncell = (size_t)m->dpad * m->n;
+        free_sparse(ctx, m);
         if (m->X && m->X != m->X32) dev_free(ctx, m->X, sizeof(__nv_bfloat16) * ncell);
         if (m->X32) dev_free(ctx, m->X32, sizeof(float) * ncell);
         if (m->Xh) dev_free(ctx, m->Xh, sizeof(__nv_bfloat16) * ncell);
@@ -360,7 +459,7 @@ lra_status lra_solve(lra_mat *mat, int k, int p, double eps, uint64_t seed, cons
             lra_mat *m;
             ~Release() { m->busy.fetch_sub(1); }
         } rel{mat};
-        Workspace ws(ctx, mat->dpad, mat->n, pmax);
+        Workspace ws(ctx, mat->dpad, mat->n, pmax, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         const lra_status st = e.solve(k, p, eps, seed, o, U, ritz, rep, nullptr);
         if (st != LRA_OK && st != LRA_ENOTCONV && rep) rep->status = st;
@@ -454,7 +553,7 @@ lra_status lra_anchor(lra_mat *mat, int p, const float *Wt, const float *B, doub
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, p);
+        Workspace ws(ctx, mat->dpad, mat->n, p, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         Padded pw(ctx, mat->dpad, p), pb(ctx, mat->dpad, p), pm(ctx, mat->dpad, p);
         pw.upload(Wt, mat->d, mat->dpad, p);
@@ -476,7 +575,7 @@ lra_status lra_xt_mul(lra_mat *mat, int p, const float *W, float *Y, int use_f32
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, p);
+        Workspace ws(ctx, mat->dpad, mat->n, p, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         Padded pw(ctx, mat->dpad, p);
         pw.upload(W, mat->d, mat->dpad, p);
@@ -499,7 +598,7 @@ lra_status lra_x_mul(lra_mat *mat, int p, const float *Y, float *G, int use_f32_
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, p);
+        Workspace ws(ctx, mat->dpad, mat->n, p, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         const int PP = pad_p(p);
         LRA_CUDA(cudaMemsetAsync(ws.Y, 0, sizeof(float) * mat->n * PP, ctx->stream));
@@ -564,7 +663,7 @@ lra_status lra_svrg_solve(lra_mat *mat, int p, const float *B, float *W, double 
     LRA_TRY({
         DeviceGuard g(ctx->device);
         const Opts o = read_opts(opt, mat->storage);
-        Workspace ws(ctx, mat->dpad, mat->n, p);
+        Workspace ws(ctx, mat->dpad, mat->n, p, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         Padded pb(ctx, mat->dpad, p), pw(ctx, mat->dpad, p);
         pb.upload(B, mat->d, mat->dpad, p);
@@ -655,7 +754,7 @@ lra_status lra_ritz(lra_mat *mat, int p, const float *S, int use_f32_copy, doubl
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, p);
+        Workspace ws(ctx, mat->dpad, mat->n, p, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         Padded ps(ctx, mat->dpad, p);
         ps.upload(S, mat->d, mat->dpad, p);
@@ -674,7 +773,7 @@ lra_status lra_lambda1_estimate(lra_mat *mat, uint64_t seed, double *lambda1_hat
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, 1);
+        Workspace ws(ctx, mat->dpad, mat->n, 1, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         *lambda1_hat = e.lambda1_estimate(seed);
         return LRA_OK;
@@ -690,7 +789,7 @@ lra_status lra_shift_tune(lra_mat *mat, uint64_t seed, double lambda1_hat, doubl
     LRA_TRY({
         DeviceGuard g(ctx->device);
         const Opts o = read_opts(opt, mat->storage);
-        Workspace ws(ctx, mat->dpad, mat->n, 1);
+        Workspace ws(ctx, mat->dpad, mat->n, 1, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         int64_t sc = solve_count ? *solve_count : 0;
         double lam = 0, inv = 0, mu = 0;
@@ -714,7 +813,7 @@ lra_status lra_delta_estimate(lra_mat *mat, int k, int p, uint64_t seed, double 
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
         DeviceGuard g(ctx->device);
-        Workspace ws(ctx, mat->dpad, mat->n, p + 1);
+        Workspace ws(ctx, mat->dpad, mat->n, p + 1, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         return e.delta_estimate(k, p, seed, *delta);
     })

@@ -81,21 +81,25 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
 // ---------------------------------------------------------------------------
 // Workspace
 // ---------------------------------------------------------------------------
-size_t workspace_bytes(int64_t dpad, int64_t n, int pmax) {
+size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
     const int PP = pad_p(pmax);
-    const int nch = xy_chunks(dpad, n);
+    const int nch = sp_items >= 0 ? 1 : std::max(xy_chunks(dpad, n, 128), xy_chunks(dpad, n, 256));
     size_t b = 0;
     b += 6 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U
     b += sizeof(float) * dpad * PP;             // Wr
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
     b += sizeof(double) * (9 * pmax * pmax + gram_scratch(pmax) + dpad);
-    b += 2 * sizeof(__nv_bfloat16) * PP * (dpad + tc_ldy(n));  // Wb Yb
+    if (sp_items >= 0)
+        b += sizeof(float) * (size_t)sp_items * PP;                 // partial
+    else
+        b += 2 * sizeof(__nv_bfloat16) * PP * (dpad + tc_ldy(n));  // Wb Yb
     return b;
 }
 
-Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream)
-    : ctx(c), dpad(dpad_), n(n_), pmax(pmax_), PPmax(pad_p(pmax_)), astream(alloc_stream) {
+Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream,
+                     int64_t sp_items_)
+    : ctx(c), dpad(dpad_), n(n_), pmax(pmax_), PPmax(pad_p(pmax_)), sp_items(sp_items_), astream(alloc_stream) {
     auto zero = [&](void *p, size_t bytes) {
         if (astream)
             LRA_CUDA(cudaMemsetAsync(p, 0, bytes, astream));
@@ -115,7 +119,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         Y = alloc<float>((size_t)n * PPmax);
         zero(Q, sizeof(float) * n * PPmax);
         zero(Y, sizeof(float) * n * PPmax);
-        nchunks = xy_chunks(dpad, n);
+        nchunks = sp_items >= 0 ? 1 : std::max(xy_chunks(dpad, n, 128), xy_chunks(dpad, n, 256));
         Gp = alloc<float>((size_t)nchunks * dpad * PPmax);
         const size_t pp = (size_t)pmax * pmax;
         H = alloc<double>(pp);
@@ -133,9 +137,13 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         status = alloc<int>(4);
         tcerr = alloc<int>(4);
         zero(tcerr, sizeof(int) * 4);
-        ldy = tc_ldy(n);
-        Wb = alloc<__nv_bfloat16>((size_t)2 * PPmax * dpad);
-        Yb = alloc<__nv_bfloat16>((size_t)2 * PPmax * ldy);
+        if (sp_items >= 0) {
+            partial = alloc<float>((size_t)std::max<int64_t>(sp_items, 1) * PPmax);
+        } else {
+            ldy = tc_ldy(n);
+            Wb = alloc<__nv_bfloat16>((size_t)2 * PPmax * dpad);
+            Yb = alloc<__nv_bfloat16>((size_t)2 * PPmax * ldy);
+        }
         LRA_CUDA(cudaMallocHost(&host, sizeof(double) * (2 * pmax + 16)));
     } catch (...) {
         for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
@@ -225,7 +233,10 @@ void Engine::ensure_norms() {
         mat_->norm2 = static_cast<double *>(dev_alloc(mat_->ctx, sizeof(double) * mat_->n));
         mat_->dev_sm = static_cast<double *>(dev_alloc(mat_->ctx, sizeof(double) * 4));
     }
-    colnorms(s_, mat_->X, mat_->storage, mat_->dpad, mat_->d, mat_->n, mat_->norm2);
+    if (mat_->sp)
+        sparse_colnorms(s_, mat_->sp->colptr, mat_->sp->cval, mat_->n, mat_->norm2);
+    else
+        colnorms(s_, mat_->X, mat_->storage, mat_->dpad, mat_->d, mat_->n, mat_->norm2);
     sum_max(s_, mat_->norm2, mat_->n, mat_->dev_sm, nullptr);
     double h[2];
     LRA_CUDA(cudaMemcpyAsync(h, mat_->dev_sm, sizeof(h), cudaMemcpyDeviceToHost, s_));
@@ -283,7 +294,12 @@ void Engine::check_tc() {
 
 void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
     const int PP = pad_p(p);
-    if (tc(use32)) {
+    if (mat_->sp) {
+        pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
+        if (timer) timer->begin(KernelTimer::XTW, p);
+        spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, ws_.Wr, PP, Y);
+        if (timer) timer->end();
+    } else if (tc(use32)) {
         pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
         if (timer) timer->begin(KernelTimer::XTW, p);
         xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, ws_.Yb,
@@ -300,15 +316,23 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
 
 void Engine::xy_pass(const float *Y32, int p, bool use32) {
     const int PP = pad_p(p);
-    if (tc(use32)) {
-        if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
+    if (mat_->sp) {
+        const auto &sp = *mat_->sp;
+        ws_.nch = 1;
         if (timer) timer->begin(KernelTimer::XY, p);
-        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp,
-              ws_.nchunks, ws_.tcerr);
+        spmm_x(s_, sp.rowptr, sp.colidx, sp.val, mat_->d, mat_->dpad, sp.item_off, sp.items, sp.nitems, kSparseSeg,
+               Y32, PP, ws_.Gp, ws_.partial);
+        if (timer) timer->end();
+    } else if (tc(use32)) {
+        if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
+        ws_.nch = xy_chunks(mat_->dpad, mat_->n, tc_rows_per_cta(PP, mat_->Xl != nullptr));
+        if (timer) timer->begin(KernelTimer::XY, p);
+        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp, ws_.nch, ws_.tcerr);
         if (timer) timer->end();
     } else {
+        ws_.nch = xy_chunks(mat_->dpad, mat_->n, 128);
         if (timer) timer->begin(KernelTimer::XY, p);
-        xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y32, PP, ws_.Gp, ws_.nchunks);
+        xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y32, PP, ws_.Gp, ws_.nch);
         if (timer) timer->end();
     }
     stats.x_passes += 1;
@@ -316,7 +340,7 @@ void Engine::xy_pass(const float *Y32, int p, bool use32) {
 
 void Engine::x_mul(const float *Y, int p, float *G, bool use32) {
     xy_pass(Y, p, use32);
-    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
+    anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
                     ws_.epi);
 }
 
@@ -328,7 +352,7 @@ void Engine::a_apply(const float *W, int p, float *G) {
         xt_mul(W, p, ws_.Y, false);
         xy_pass(ws_.Y, p, false);
     }
-    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
+    anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
                     ws_.epi);
 }
 
@@ -344,7 +368,7 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
         xt_mul(Wt, p, ws_.Y, false);
         xy_pass(ws_.Y, p, false);
     }
-    anchor_epilogue(s_, ws_.Gp, ws_.nchunks, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
+    anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
     if (nM2 || nB2) {
         LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
         if (tc(false)) check_tc();
@@ -356,6 +380,17 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
 
 void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
                    const float *cval, int64_t m, double eta, double lam) {
+    if (mat_->sp) {
+        // factored form: Mr = M row-major in Wr, Z in the G buffer (both free
+        // between the anchor's epilogue and the next X pass)
+        const int PP = pad_p(p);
+        pack_rm(s_, M, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
+        if (timer) timer->begin(KernelTimer::INNER, p);
+        svrg_inner_csc(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->dpad, p, PP, W, Wt, ws_.Wr,
+                       ws_.Gp, ws_.dots, idx, cval, m, eta, lam);
+        if (timer) timer->end();
+        return;
+    }
     if (timer) timer->begin(KernelTimer::INNER, p);
     svrg_inner(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, p, W, Wt, M, idx, cval, m,
                (float)eta, (float)lam);

@@ -36,6 +36,16 @@ struct lra_mat {
     // FP32 storage: BF16 pair (x = hi + lo + r, |r| <= 2^-17 |x|) streamed by the
     // tensor-core X passes; null for BF16 storage
     __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
+    // sparse X (X == nullptr): CSR of the d rows, compressed columns x_i, and
+    // the row work list of X Y (item = (row, segment of kSparseSeg entries))
+    struct Sparse {
+        int64_t nnz = 0, nitems = 0;
+        int64_t *rowptr = nullptr, *colptr = nullptr, *item_off = nullptr;
+        int32_t *colidx = nullptr, *rowidx = nullptr;
+        float *val = nullptr, *cval = nullptr;
+        int2 *items = nullptr;
+    };
+    Sparse *sp = nullptr;
     // setup cache (a0)
     std::mutex setup_mu;
     bool have_norms = false;
@@ -116,7 +126,8 @@ struct Workspace {
     int pmax = 0, PPmax = 0;
     float *S = nullptr, *W = nullptr, *Wt = nullptr, *M = nullptr, *T1 = nullptr, *U = nullptr;
     float *Wr = nullptr, *Q = nullptr, *Y = nullptr, *Gp = nullptr;
-    int nchunks = 0;
+    int nchunks = 0;  // capacity of Gp in dpad x PP chunks
+    int nch = 1;      // chunks written by the last X Y pass
     double *H = nullptr, *Hc = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;
@@ -134,7 +145,13 @@ struct Workspace {
     // stream (no device-wide synchronisation on free; used by the request loop)
     cudaStream_t astream = nullptr;
 
-    Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream = nullptr);
+    float *partial = nullptr;  // sparse X: per-segment rows of X Y (nitems x PP)
+    int64_t sp_items = -1;
+
+    // sp_items >= 0: buffers of a sparse X with that many row items (one G
+    // chunk, no BF16 operands); -1: dense X
+    Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStream_t alloc_stream = nullptr,
+              int64_t sp_items_ = -1);
     ~Workspace();
     void ensure_idx(int64_t m);
     template <typename T>
@@ -146,7 +163,9 @@ struct Workspace {
     }
 };
 
-size_t workspace_bytes(int64_t dpad, int64_t n, int pmax);
+size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items = -1);
+// the sp_items argument of a workspace for X products on `m`
+inline int64_t ws_items(const lra_mat *m) { return m->sp ? m->sp->nitems : -1; }
 
 class Engine {
    public:
@@ -193,7 +212,9 @@ class Engine {
    private:
     // tensor-core passes: BF16 X, or the BF16 pair of an FP32 X; the exact FP32
     // values (use32) go through the CUDA-core kernels
-    bool tc(bool use32) const { return !use32 && (mat_->storage == LRA_BF16 || mat_->Xh != nullptr); }
+    bool tc(bool use32) const {
+        return !use32 && !mat_->sp && (mat_->storage == LRA_BF16 || mat_->Xh != nullptr);
+    }
     const __nv_bfloat16 *tcx() const {
         return mat_->Xh ? mat_->Xh : static_cast<const __nv_bfloat16 *>(mat_->X);
     }

@@ -418,11 +418,26 @@ void xtw(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad,
     });
 }
 
-int xy_chunks(int64_t dpad, int64_t n) {
-    const int64_t row_tiles = dpad / kTR;
-    const int64_t want = ceil_div(152 * 4, row_tiles);
-    const int64_t maxc = std::max<int64_t>(1, ceil_div(n, 4 * kKC));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, maxc));
+// Split of the n columns for the X Y passes: the grid is (row tiles) x
+// chunks with one resident CTA per SM, so the chunk count is chosen to fill
+// whole waves of 152 SMs: the smallest count giving at least two waves at >= 97%
+// occupancy of the last one, else the best-filled count up to 64 chunks.
+int xy_chunks(int64_t dpad, int64_t n, int rows_per_cta) {
+    const int64_t row_tiles = ceil_div(dpad, rows_per_cta);
+    const int64_t maxc = std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(n, 4 * kKC)));
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int64_t c = 1; c <= maxc; ++c) {
+        const int64_t units = row_tiles * c;
+        const int64_t waves = ceil_div(units, 152);
+        const double eff = (double)units / (double)(waves * 152);
+        if (units >= 2 * 152 && eff >= 0.97) return (int)c;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = c;
+        }
+    }
+    return (int)best;
 }
 
 void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int64_t n,

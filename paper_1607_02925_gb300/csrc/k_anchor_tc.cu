@@ -26,7 +26,7 @@ using namespace tc;
 constexpr int kBM = 128;                // rows of the MMA tile
 constexpr int kBK = 64;                 // K elements per pipeline stage (128 B of BF16)
 constexpr int kATile = kBM * kBK * 2;   // 16 KB
-constexpr int kTmemCols = 128;          // accumulator columns allocated (PP <= 112)
+constexpr int kAccCols = 128;           // TMEM columns per accumulator (PP <= 112)
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -34,13 +34,21 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 
 // NA = 1: X stored in BF16.  NA = 2: X stored in FP32 and streamed as its
 // BF16 hi + lo pair (x = hi + lo + r, |r| <= 2^-17 |x|).
-template <int PP, int NA>
+// MT = number of 128-row M tiles per CTA sharing each small-operand tile (two
+// accumulators in TMEM): halves the small operand's L2 traffic and doubles the
+// X bytes in flight per stage.
+template <int PP, int NA, int MT>
 struct Tile {
-    static constexpr int kA = NA * kATile;
+    static constexpr int kA1 = NA * kATile;         // one M tile: hi [+ lo]
+    static constexpr int kA = MT * kA1;
     static constexpr int kB = PP * 128;             // one of hi / lo: PP rows x 128 B
     static constexpr int kStage = kA + 2 * kB;      // multiple of 1024
-    static constexpr int kStages = NA == 1 ? (PP <= 64 ? 3 : 4) : (kStage <= 50 * 1024 ? 4 : 3);
+    static constexpr int kFit = (220 * 1024) / kStage;
+    static constexpr int kStages = MT == 1 ? (NA == 1 ? (PP <= 64 ? 3 : 4) : (kStage <= 50 * 1024 ? 4 : 3))
+                                           : (kFit > 4 ? 4 : kFit);
     static constexpr int kSmem = kStages * kStage + 1024 + 256;
+    static constexpr uint32_t kTmemCols = MT == 1 ? 128u : 256u;
+    static_assert(kStages >= 2, "pipeline needs two stages");
 };
 
 // Shared tail of both kernels: barriers and the TMEM address slot after the stages.
@@ -52,19 +60,19 @@ struct Ctl {
 // ---------------------------------------------------------------------------
 // Y = X^T W
 // ---------------------------------------------------------------------------
-template <int PP, int NA>
+template <int PP, int NA, int MT>
 __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                                                         const __grid_constant__ CUtensorMap tmXl,
                                                         const __grid_constant__ CUtensorMap tmW,
                                                         int nkb, int64_t n, float *__restrict__ Y32,
                                                         __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
                                                         int *__restrict__ err) {
-    using T = Tile<PP, NA>;
+    using T = Tile<PP, NA, MT>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i0 = (int64_t)blockIdx.x * kBM;
+    const int64_t i0 = (int64_t)blockIdx.x * kBM * MT;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < T::kStages; ++s) {
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
         prefetch_tmap(&tmW);
     }
     if (warp == 0) {
-        tmem_alloc(&ctl->tmem, kTmemCols);
+        tmem_alloc(&ctl->tmem, T::kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -97,8 +105,12 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
             }
             uint8_t *a = smem + st * T::kStage;
             mbar_expect_tx(&ctl->full[st], T::kStage);
-            tma_load_2d(a, &tmX, kb * kBK, (int)i0, &ctl->full[st]);
-            if (NA == 2) tma_load_2d(a + kATile, &tmXl, kb * kBK, (int)i0, &ctl->full[st]);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int row = (int)i0 + mt * kBM;
+                tma_load_2d(a + mt * T::kA1, &tmX, kb * kBK, row, &ctl->full[st]);
+                if (NA == 2) tma_load_2d(a + mt * T::kA1 + kATile, &tmXl, kb * kBK, row, &ctl->full[st]);
+            }
             tma_load_2d(a + T::kA, &tmW, kb * kBK, 0, &ctl->full[st]);
             tma_load_2d(a + T::kA + T::kB, &tmW, kb * kBK, PP, &ctl->full[st]);
         }
@@ -117,11 +129,17 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
             const uint32_t bh = a + T::kA, bl = bh + T::kB;
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks) {
-                const uint64_t ad = sw128_desc(a + ks * 32, 16, 1024);
                 const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                mma_f16(tmem, ad, bhd, idesc, (kb | ks) != 0);
-                mma_f16(tmem, ad, sw128_desc(bl + ks * 32, 16, 1024), idesc, 1u);
-                if (NA == 2) mma_f16(tmem, sw128_desc(a + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+                const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint32_t am = a + mt * T::kA1;
+                    const uint32_t acc = tmem + mt * kAccCols;
+                    const uint64_t ad = sw128_desc(am + ks * 32, 16, 1024);
+                    mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
+                    mma_f16(acc, ad, bld, idesc, 1u);
+                    if (NA == 2) mma_f16(acc, sw128_desc(am + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+                }
             }
             mma_commit(&ctl->empty[st]);
         }
@@ -129,14 +147,16 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
     }
     __syncwarp();
 
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows i0 + 32w + lane)
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows i0 + 128 mt + 32w + lane)
     const bool ok = mbar_wait(&ctl->accum, 0);
     tc_fence_after();
     if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
     } else {
-        const int64_t i = i0 + warp * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int64_t i = i0 + mt * kBM + warp * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + mt * kAccCols;
 #pragma unroll
         for (int c = 0; c < PP; c += 16) {
             float v[16];
@@ -158,27 +178,28 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
                 }
             }
         }
+      }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc(tmem, T::kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
 // Partial G = X[rows, chunk] Y[chunk, :]  (X is the MN-major operand here)
 // ---------------------------------------------------------------------------
-template <int PP, int NA>
+template <int PP, int NA, int MT>
 __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                                                        const __grid_constant__ CUtensorMap tmXl,
                                                        const __grid_constant__ CUtensorMap tmY,
                                                        int64_t cols_per_chunk, int64_t n, int64_t dpad,
                                                        float *__restrict__ Gp, int *__restrict__ err) {
-    using T = Tile<PP, NA>;
+    using T = Tile<PP, NA, MT>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * kBM;
+    const int64_t r0 = (int64_t)blockIdx.x * kBM * MT;
     const int64_t c0 = (int64_t)blockIdx.y * cols_per_chunk;
     const int64_t c1 = (c0 + cols_per_chunk < n) ? c0 + cols_per_chunk : n;
     const int nkb = c1 > c0 ? (int)((c1 - c0 + kBK - 1) / kBK) : 0;
@@ -195,7 +216,7 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
         prefetch_tmap(&tmY);
     }
     if (warp == 0) {
-        tmem_alloc(&ctl->tmem, kTmemCols);
+        tmem_alloc(&ctl->tmem, T::kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -214,11 +235,17 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
             uint8_t *a = smem + st * T::kStage;
             const int col = (int)(c0 + (int64_t)kb * kBK);
             mbar_expect_tx(&ctl->full[st], T::kStage);
-            tma_load_2d(a, &tmX, (int)r0, col, &ctl->full[st]);
-            tma_load_2d(a + kATile / 2, &tmX, (int)r0 + 64, col, &ctl->full[st]);
-            if (NA == 2) {
-                tma_load_2d(a + kATile, &tmXl, (int)r0, col, &ctl->full[st]);
-                tma_load_2d(a + kATile + kATile / 2, &tmXl, (int)r0 + 64, col, &ctl->full[st]);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                // rows past dpad (an odd number of 128-row tiles) read as zeros
+                const int row = (int)r0 + mt * kBM;
+                uint8_t *am = a + mt * T::kA1;
+                tma_load_2d(am, &tmX, row, col, &ctl->full[st]);
+                tma_load_2d(am + kATile / 2, &tmX, row + 64, col, &ctl->full[st]);
+                if (NA == 2) {
+                    tma_load_2d(am + kATile, &tmXl, row, col, &ctl->full[st]);
+                    tma_load_2d(am + kATile + kATile / 2, &tmXl, row + 64, col, &ctl->full[st]);
+                }
             }
             tma_load_2d(a + T::kA, &tmY, col, 0, &ctl->full[st]);
             tma_load_2d(a + T::kA + T::kB, &tmY, col, PP, &ctl->full[st]);
@@ -237,12 +264,19 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
             const uint32_t bh = a + T::kA, bl = bh + T::kB;
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks) {
-                // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
-                const uint64_t ad = sw128_desc(a + ks * 2048, kATile / 2, 1024);
                 const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                mma_f16(tmem, ad, bhd, idesc, (kb | ks) != 0);
-                mma_f16(tmem, ad, sw128_desc(bl + ks * 32, 16, 1024), idesc, 1u);
-                if (NA == 2) mma_f16(tmem, sw128_desc(a + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
+                    const uint32_t am = a + mt * T::kA1;
+                    const uint32_t acc = tmem + mt * kAccCols;
+                    const uint64_t ad = sw128_desc(am + ks * 2048, kATile / 2, 1024);
+                    mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
+                    mma_f16(acc, ad, bld, idesc, 1u);
+                    if (NA == 2)
+                        mma_f16(acc, sw128_desc(am + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                }
             }
             mma_commit(&ctl->empty[st]);
         }
@@ -252,12 +286,14 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
 
     const bool ok = mbar_wait(&ctl->accum, 0);
     tc_fence_after();
-    const int64_t r = r0 + warp * 32 + lane;
-    float *out = Gp + (int64_t)blockIdx.y * dpad * PP + r * PP;
     if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
     } else {
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int64_t r = r0 + mt * kBM + warp * 32 + lane;
+        float *out = Gp + (int64_t)blockIdx.y * dpad * PP + r * PP;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + mt * kAccCols;
 #pragma unroll
         for (int c = 0; c < PP; c += 16) {
             float v[16];
@@ -267,14 +303,18 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
 #pragma unroll
                 for (int q = 0; q < 16; ++q) v[q] = 0.0f;
             }
-            float4 *dst = reinterpret_cast<float4 *>(out + c);
+            if (r < dpad) {
+                float4 *dst = reinterpret_cast<float4 *>(out + c);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 4; ++q)
+                    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
         }
+      }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc(tmem, T::kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -392,23 +432,28 @@ void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh
     LRA_LAUNCHED();
 }
 
+int tc_rows_per_cta(int PP, bool pair) { return (!pair && PP >= 64) ? 2 * kBM : kBM; }
+
 void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
             const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err) {
     const CUtensorMap mx = make_map(X, dpad, n, dpad, kBK, kBM);
     const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, kBK, kBM);
     const CUtensorMap mw = make_map(Wb, dpad, 2 * PP, dpad, kBK, PP);
     const int nkb = (int)(dpad / kBK);
+    const int rows = tc_rows_per_cta(PP, Xl != nullptr);
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<(unsigned)ceil_div(n, kBM), 128, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
+            kern<<<(unsigned)ceil_div(n, rows), 128, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
             LRA_LAUNCHED();
         };
         if (Xl)
-            launch(xtw_tc_kernel<P, 2>, Tile<P, 2>::kSmem);
+            launch(xtw_tc_kernel<P, 2, 1>, Tile<P, 2, 1>::kSmem);
+        else if (rows == kBM)
+            launch(xtw_tc_kernel<P, 1, 1>, Tile<P, 1, 1>::kSmem);
         else
-            launch(xtw_tc_kernel<P, 1>, Tile<P, 1>::kSmem);
+            launch(xtw_tc_kernel<P, 1, 2>, Tile<P, 1, 2>::kSmem);
     });
 }
 
@@ -418,18 +463,21 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
     const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, 64, kBK);
     const CUtensorMap my = make_map(Yb, n, 2 * PP, ldy, kBK, PP);
     const int64_t cpc = round_up(ceil_div(n, nchunks), kBK);
+    const int rows = tc_rows_per_cta(PP, Xl != nullptr);
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
-        const dim3 grid((unsigned)(dpad / kBM), (unsigned)nchunks);
+        const dim3 grid((unsigned)ceil_div(dpad, rows), (unsigned)nchunks);
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
             kern<<<grid, 128, smem, s>>>(mx, mxl, my, cpc, n, dpad, Gp, err);
             LRA_LAUNCHED();
         };
         if (Xl)
-            launch(xy_tc_kernel<P, 2>, Tile<P, 2>::kSmem);
+            launch(xy_tc_kernel<P, 2, 1>, Tile<P, 2, 1>::kSmem);
+        else if (rows == kBM)
+            launch(xy_tc_kernel<P, 1, 1>, Tile<P, 1, 1>::kSmem);
         else
-            launch(xy_tc_kernel<P, 1>, Tile<P, 1>::kSmem);
+            launch(xy_tc_kernel<P, 1, 2>, Tile<P, 1, 2>::kSmem);
     });
 }
 

@@ -1,0 +1,599 @@
+// Sparse X (d x n, FP32 values) on the device: validation of the caller's CSR
+// of the rows of X, the compressed columns x_i built from it (a stable
+// transpose: counting sort by column, then each column sorted by row), the
+// row work list of the X Y product, and the kernels of the anchor pass
+// (Sec. 2.3: Y = X^T W over the columns, G = X Y over the rows), of the column
+// norms (a0) and of the SVRG inner loop in factored form.
+//
+// Every reduction runs in a fixed order, so results do not depend on timing:
+// the transpose's atomic cursor only decides where an entry lands before its
+// column is sorted by (unique) row index.
+#include <algorithm>
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace lra {
+
+namespace {
+
+constexpr int kWarps = 8;  // warps per CTA of the warp-per-row/column kernels
+
+__device__ __forceinline__ int64_t global_warp() {
+    return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ int64_t warps_in_grid() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
+
+unsigned grid_for(int64_t items, int per_block) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(items, per_block), 152 * 16));
+}
+
+// ---------------------------------------------------------------------------
+// Validation: bit 1 row pointer out of order or range, 2 column index out of
+// [0, n), 4 column indices not strictly increasing within a row, 8 a value
+// not finite, 16 rowptr[0] != 0 or rowptr[d] != nnz.
+// ---------------------------------------------------------------------------
+__global__ void csr_check_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                 const float *__restrict__ val, int64_t d, int64_t n, int64_t nnz,
+                                 int *__restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rowptr[0] != 0 || rowptr[d] != nnz) atomicOr(bad, 16);
+    }
+    int flags = 0;
+    for (int64_t r = global_warp(); r < d; r += warps_in_grid()) {
+        const int64_t lo = rowptr[r], hi = rowptr[r + 1];
+        if (lo < 0 || hi < lo || hi > nnz) {
+            flags |= 1;
+            continue;
+        }
+        for (int64_t k = lo + lane; k < hi; k += 32) {
+            const int32_t c = colidx[k];
+            if (c < 0 || (int64_t)c >= n) flags |= 2;
+            if (k + 1 < hi && colidx[k + 1] <= c) flags |= 4;
+            if (!isfinite(val[k])) flags |= 8;
+        }
+    }
+    if (flags) atomicOr(bad, flags);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int64 counts: out[0] = 0, out[i + 1] = in[0] + ... + in[i].
+// Tiles of 1024 (one element per thread), tile totals scanned by one CTA.
+// ---------------------------------------------------------------------------
+constexpr int kScanTile = 1024;
+
+__device__ int64_t block_incl_scan(int64_t v, int64_t *warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int64_t s = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_tot[lane] = s;
+    }
+    __syncthreads();
+    if (w > 0) v += warp_tot[w - 1];
+    return v;
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_tiles_kernel(const int64_t *__restrict__ in, int64_t N,
+                                                               int64_t *__restrict__ out,
+                                                               int64_t *__restrict__ tile_tot) {
+    __shared__ int64_t wt[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+    const int64_t v = block_incl_scan(i < N ? in[i] : 0, wt);
+    if (i < N) out[i + 1] = v;
+    if (threadIdx.x == kScanTile - 1) tile_tot[blockIdx.x] = v;
+}
+
+// one CTA: exclusive scan of the tile totals, in chunks of 1024 with a carry
+__global__ void __launch_bounds__(kScanTile) scan_totals_kernel(int64_t *__restrict__ tile_tot, int64_t T) {
+    __shared__ int64_t wt[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < T; base += kScanTile) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < T ? tile_tot[i] : 0;
+        const int64_t incl = block_incl_scan(v, wt);
+        const int64_t c = carry;
+        if (i < T) tile_tot[i] = c + incl - v;  // exclusive
+        __syncthreads();
+        if (threadIdx.x == kScanTile - 1) carry = c + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_add_kernel(int64_t *__restrict__ out, int64_t N, const int64_t *__restrict__ tile_off) {
+    const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+    if (i < N) out[i + 1] += tile_off[blockIdx.x];
+    if (i == 0) out[0] = 0;
+}
+
+// scratch >= ceil(N / 1024) int64
+void exclusive_scan(cudaStream_t s, const int64_t *in, int64_t N, int64_t *out, int64_t *scratch) {
+    const int64_t T = std::max<int64_t>(1, ceil_div(N, kScanTile));
+    scan_tiles_kernel<<<(unsigned)T, kScanTile, 0, s>>>(in, N, out, scratch);
+    LRA_LAUNCHED();
+    scan_totals_kernel<<<1, kScanTile, 0, s>>>(scratch, T);
+    LRA_LAUNCHED();
+    scan_add_kernel<<<(unsigned)T, kScanTile, 0, s>>>(out, N, scratch);
+    LRA_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------
+// Transpose: column counts, scatter through per-column cursors, column sort.
+// ---------------------------------------------------------------------------
+__global__ void col_count_kernel(const int32_t *__restrict__ colidx, int64_t nnz,
+                                 unsigned long long *__restrict__ cnt) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[colidx[k]], 1ull);
+}
+
+__global__ void col_scatter_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                   const float *__restrict__ val, int64_t d,
+                                   const int64_t *__restrict__ colptr, int *__restrict__ cursor,
+                                   int32_t *__restrict__ rowidx, float *__restrict__ cval) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = global_warp(); r < d; r += warps_in_grid()) {
+        const int64_t lo = rowptr[r], hi = rowptr[r + 1];
+        for (int64_t k = lo + lane; k < hi; k += 32) {
+            const int32_t c = colidx[k];
+            const int64_t pos = colptr[c] + atomicAdd(&cursor[c], 1);
+            rowidx[pos] = (int32_t)r;
+            cval[pos] = val[k];
+        }
+    }
+}
+
+// Ascending sort network for any length L (all comparators put the smaller key
+// at the lower index; positions >= L act as +infinity and are never touched):
+// for size = 2, 4, ... : compare i with its mirror in the size-block, then
+// i with i + h for h = size/4, ..., 1.  `step(i, j)` is called for i < j < L.
+template <bool kBlock>
+__device__ __forceinline__ void net_sync() {
+    if (kBlock)
+        __syncthreads();
+    else
+        __syncwarp();
+}
+
+template <bool kBlock, typename F>
+__device__ __forceinline__ void sort_network(int64_t L, int tid, int nthr, F &&step) {
+    int64_t N = 1;
+    while (N < L) N <<= 1;
+    for (int64_t size = 2; size <= N; size <<= 1) {
+        const int64_t half = size >> 1;
+        for (int64_t t = tid; t < (N >> 1); t += nthr) {
+            const int64_t blk = t / half, off = t - blk * half;
+            const int64_t i = blk * size + off, j = blk * size + size - 1 - off;
+            if (j < L) step(i, j);
+        }
+        net_sync<kBlock>();
+        for (int64_t h = half >> 1; h > 0; h >>= 1) {
+            for (int64_t t = tid; t < (N >> 1); t += nthr) {
+                const int64_t i = (t / h) * 2 * h + (t % h), j = i + h;
+                if (j < L) step(i, j);
+            }
+            net_sync<kBlock>();
+        }
+    }
+}
+
+constexpr int kSortWarp = 1024;  // longest column sorted by one warp in shared memory
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSortWarps) sort_cols_warp_kernel(const int64_t *__restrict__ colptr,
+                                                                        int64_t n, int32_t *__restrict__ rowidx,
+                                                                        float *__restrict__ cval) {
+    __shared__ int32_t ks[kSortWarps][kSortWarp];
+    __shared__ float vs[kSortWarps][kSortWarp];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *K = ks[w];
+    float *V = vs[w];
+    for (int64_t c = global_warp(); c < n; c += warps_in_grid()) {
+        const int64_t lo = colptr[c], L = colptr[c + 1] - lo;
+        if (L < 2 || L > kSortWarp) continue;
+        for (int64_t e = lane; e < L; e += 32) {
+            K[e] = rowidx[lo + e];
+            V[e] = cval[lo + e];
+        }
+        __syncwarp();
+        auto step = [&](int64_t i, int64_t j) {
+            if (K[i] > K[j]) {
+                const int32_t tk = K[i];
+                K[i] = K[j];
+                K[j] = tk;
+                const float tv = V[i];
+                V[i] = V[j];
+                V[j] = tv;
+            }
+        };
+        sort_network<false>(L, lane, 32, step);
+        for (int64_t e = lane; e < L; e += 32) {
+            rowidx[lo + e] = K[e];
+            cval[lo + e] = V[e];
+        }
+        __syncwarp();
+    }
+}
+
+// columns longer than kSortWarp: one CTA per column, in place in global memory
+__global__ void __launch_bounds__(512) sort_cols_block_kernel(const int64_t *__restrict__ colptr, int64_t n,
+                                                              int32_t *__restrict__ rowidx,
+                                                              float *__restrict__ cval) {
+    for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+        const int64_t lo = colptr[c], L = colptr[c + 1] - lo;
+        if (L <= kSortWarp) continue;
+        int32_t *K = rowidx + lo;
+        float *V = cval + lo;
+        auto step = [&](int64_t i, int64_t j) {
+            const int32_t ki = K[i], kj = K[j];
+            if (ki > kj) {
+                K[i] = kj;
+                K[j] = ki;
+                const float tv = V[i];
+                V[i] = V[j];
+                V[j] = tv;
+            }
+        };
+        sort_network<true>(L, threadIdx.x, blockDim.x, step);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row work list of X Y: row r of X is cut into ceil(len/seg) segments (one for
+// empty rows and the padding rows d..dpad-1); item j = (row, segment).
+// ---------------------------------------------------------------------------
+__global__ void row_segs_kernel(const int64_t *__restrict__ rowptr, int64_t d, int64_t dpad, int seg,
+                                int64_t *__restrict__ nseg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dpad; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = 1;
+        if (r < d) {
+            s = ceil_div(rowptr[r + 1] - rowptr[r], seg);
+            if (s < 1) s = 1;
+        }
+        nseg[r] = s;
+    }
+}
+
+__global__ void fill_items_kernel(const int64_t *__restrict__ item_off, int64_t dpad, int2 *__restrict__ items) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dpad; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = item_off[r], e = item_off[r + 1];
+        for (int64_t j = o; j < e; ++j) items[j] = make_int2((int)r, (int)(j - o));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column norms ||x_i||^2 in FP64 (warp per column, fixed order)
+// ---------------------------------------------------------------------------
+__global__ void sparse_colnorms_kernel(const int64_t *__restrict__ colptr, const float *__restrict__ cval,
+                                       int64_t n, double *__restrict__ norm2) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = global_warp(); i < n; i += warps_in_grid()) {
+        double acc = 0.0;
+        for (int64_t k = colptr[i] + lane; k < colptr[i + 1]; k += 32) {
+            const double v = cval[k];
+            acc = fma(v, v, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) norm2[i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather-accumulate of one compressed line: acc[q] += v_k * B[idx_k * PP + lane + 32 q]
+// over k in [lo, hi), entries broadcast from lane-cooperative loads.
+// ---------------------------------------------------------------------------
+template <int NQ>
+__device__ __forceinline__ void gather_line(const int32_t *__restrict__ idx, const float *__restrict__ vals,
+                                            int64_t lo, int64_t hi, const float *__restrict__ B, int PP,
+                                            int lane, float (&acc)[NQ]) {
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t k = base + lane;
+        const int32_t rr = k < hi ? idx[k] : 0;
+        const float vv = k < hi ? vals[k] : 0.0f;
+        const int cnt = (int)((hi - base) < 32 ? (hi - base) : 32);
+#pragma unroll 4
+        for (int e = 0; e < cnt; ++e) {
+            const int64_t r = __shfl_sync(0xffffffffu, rr, e);
+            const float v = __shfl_sync(0xffffffffu, vv, e);
+            const float *row = B + r * PP;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < PP) acc[q] = fmaf(v, __ldg(row + j), acc[q]);
+            }
+        }
+    }
+}
+
+// Y (n x PP row-major) = X^T Wr: warp per column x_i
+template <int NQ>
+__global__ void __launch_bounds__(32 * kWarps) spmm_xt_kernel(const int64_t *__restrict__ colptr,
+                                                              const int32_t *__restrict__ rowidx,
+                                                              const float *__restrict__ cval, int64_t n,
+                                                              const float *__restrict__ Wr, int PP,
+                                                              float *__restrict__ Y) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = global_warp(); i < n; i += warps_in_grid()) {
+        float acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
+        gather_line<NQ>(rowidx, cval, colptr[i], colptr[i + 1], Wr, PP, lane, acc);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = lane + 32 * q;
+            if (j < PP) Y[i * PP + j] = acc[q];
+        }
+    }
+}
+
+// G rows (dpad x PP row-major) = X Y over the row work list: single-segment rows
+// go straight to G, segments of long rows to partial[item]
+template <int NQ>
+__global__ void __launch_bounds__(32 * kWarps) spmm_x_kernel(const int64_t *__restrict__ rowptr,
+                                                             const int32_t *__restrict__ colidx,
+                                                             const float *__restrict__ val, int64_t d,
+                                                             const int64_t *__restrict__ item_off,
+                                                             const int2 *__restrict__ items, int64_t nitems,
+                                                             int seg, const float *__restrict__ Y, int PP,
+                                                             float *__restrict__ G, float *__restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t it = global_warp(); it < nitems; it += warps_in_grid()) {
+        const int2 rs = items[it];
+        const int64_t r = rs.x;
+        int64_t lo = 0, hi = 0;
+        if (r < d) {
+            lo = rowptr[r] + (int64_t)rs.y * seg;
+            hi = rowptr[r + 1];
+            if (hi > lo + seg) hi = lo + seg;
+        }
+        float acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
+        gather_line<NQ>(colidx, val, lo, hi, Y, PP, lane, acc);
+        const bool single = (item_off[r + 1] - item_off[r]) == 1;
+        float *dst = single ? G + r * PP : partial + it * PP;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = lane + 32 * q;
+            if (j < PP) dst[j] = acc[q];
+        }
+    }
+}
+
+// long rows: G[r] = sum of its segments in order
+__global__ void __launch_bounds__(32 * kWarps) long_rows_kernel(const int64_t *__restrict__ item_off, int64_t dpad,
+                                                                const float *__restrict__ partial, int PP,
+                                                                float *__restrict__ G) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = global_warp(); r < dpad; r += warps_in_grid()) {
+        const int64_t o = item_off[r], e = item_off[r + 1];
+        if (e - o < 2) continue;
+        for (int j = lane; j < PP; j += 32) {
+            float a = 0.0f;
+            for (int64_t t = o; t < e; ++t) a += partial[t * PP + j];
+            G[r * PP + j] = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SVRG inner loop in factored form (sparse X).  W - Wt = a Z + b M, so a step
+// with column x_i (c = c_i) is
+//     r = a (x_i^T Z) + b (x_i^T M),  a' = (1 - eta lambda) a,
+//     b' = (1 - eta lambda) b - eta,  Z[rows of x_i] += (eta c / a') x_i r,
+// and Z is rescaled (Z <- a Z, a <- 1) once a < 2^-30.  One CTA runs the
+// chain; warp w takes the entries w, w + 8, ... of the column, lanes the columns
+// of the block (row-major Z and M, PP wide).
+// ---------------------------------------------------------------------------
+__global__ void zdiff_kernel(const float *__restrict__ W, const float *__restrict__ Wt, int64_t dpad, int p, int PP,
+                             float *__restrict__ Z) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < dpad * PP; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / PP;
+        const int j = (int)(e - r * PP);
+        Z[e] = j < p ? W[r + (int64_t)j * dpad] - Wt[r + (int64_t)j * dpad] : 0.0f;
+    }
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *__restrict__ colptr,
+                                                                const int32_t *__restrict__ rowidx,
+                                                                const float *__restrict__ cval, int64_t dpad, int PP,
+                                                                const float *__restrict__ Mr, float *__restrict__ Z,
+                                                                const int32_t *__restrict__ idx,
+                                                                const float *__restrict__ cvals, int64_t m, double eta,
+                                                                double lam, double *__restrict__ ab) {
+    __shared__ float redz[kWarps][32 * NQ], redm[kWarps][32 * NQ];
+    __shared__ float rv[32 * NQ];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double g = 1.0 - eta * lam;
+    double a = 1.0, b = 0.0;
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t i = idx[t];
+        const int64_t lo = colptr[i], hi = colptr[i + 1];
+        float sz[NQ], sm[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sz[q] = sm[q] = 0.0f;
+        for (int64_t k = lo + w; k < hi; k += kWarps) {
+            const int64_t r = rowidx[k];
+            const float v = cval[k];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < PP) {
+                    sz[q] = fmaf(v, Z[r * PP + j], sz[q]);
+                    sm[q] = fmaf(v, __ldg(Mr + r * PP + j), sm[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            redz[w][lane + 32 * q] = sz[q];
+            redm[w][lane + 32 * q] = sm[q];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32 * NQ) {
+            float z = 0.0f, mm = 0.0f;
+#pragma unroll
+            for (int u = 0; u < kWarps; ++u) {
+                z += redz[u][threadIdx.x];
+                mm += redm[u][threadIdx.x];
+            }
+            rv[threadIdx.x] = (float)(a * (double)z + b * (double)mm);
+        }
+        __syncthreads();
+        const double a1 = g * a;
+        b = g * b - eta;
+        const float coef = (float)(eta * (double)cvals[t] / a1);
+        for (int64_t k = lo + w; k < hi; k += kWarps) {
+            const int64_t r = rowidx[k];
+            const float cv = coef * cval[k];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < PP) Z[r * PP + j] = fmaf(cv, rv[j], Z[r * PP + j]);
+            }
+        }
+        a = a1;
+        if (a < 0x1p-30) {
+            __syncthreads();
+            const float af = (float)a;
+            for (int64_t e = threadIdx.x; e < dpad * PP; e += blockDim.x) Z[e] *= af;
+            a = 1.0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ab[0] = a;
+        ab[1] = b;
+    }
+}
+
+__global__ void inner_final_kernel(const float *__restrict__ Wt, const float *__restrict__ Z,
+                                   const float *__restrict__ Mr, const double *__restrict__ ab, int64_t dpad, int p,
+                                   int PP, float *__restrict__ W) {
+    const float a = (float)ab[0], b = (float)ab[1];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < dpad * p; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / dpad, r = e - j * dpad;
+        W[e] = Wt[e] + a * Z[r * PP + j] + b * Mr[r * PP + j];
+    }
+}
+
+template <typename F>
+void dispatch_nq(int PP, F &&f) {
+    switch (ceil_div(PP, 32)) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        default:
+            set_error("sparse kernels support at most 128 block columns");
+            throw Error{LRA_EINVAL};
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void csr_check(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+               int64_t n, int64_t nnz, int *bad) {
+    LRA_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    csr_check_kernel<<<grid_for(d, kWarps), 32 * kWarps, 0, s>>>(rowptr, colidx, val, d, n, nnz, bad);
+    LRA_LAUNCHED();
+}
+
+int64_t sparse_scan_scratch(int64_t N) { return ceil_div(std::max<int64_t>(N, 1), kScanTile) + 8; }
+
+void csr_transpose(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+                   int64_t n, int64_t nnz, int64_t *colptr, int32_t *rowidx, float *cval, int64_t *cnt,
+                   int *cursor, int64_t *scan_scratch) {
+    LRA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * n, s));
+    LRA_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * n, s));
+    if (nnz > 0) {
+        col_count_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(colidx, nnz, reinterpret_cast<unsigned long long *>(cnt));
+        LRA_LAUNCHED();
+    }
+    exclusive_scan(s, cnt, n, colptr, scan_scratch);
+    if (nnz == 0) return;
+    col_scatter_kernel<<<grid_for(d, kWarps), 32 * kWarps, 0, s>>>(rowptr, colidx, val, d, colptr, cursor, rowidx,
+                                                                   cval);
+    LRA_LAUNCHED();
+    sort_cols_warp_kernel<<<grid_for(n, kSortWarps), 32 * kSortWarps, 0, s>>>(colptr, n, rowidx, cval);
+    LRA_LAUNCHED();
+    sort_cols_block_kernel<<<152, 512, 0, s>>>(colptr, n, rowidx, cval);
+    LRA_LAUNCHED();
+}
+
+void sparse_row_items(cudaStream_t s, const int64_t *rowptr, int64_t d, int64_t dpad, int seg, int64_t *nseg,
+                      int64_t *item_off, int64_t *scan_scratch) {
+    row_segs_kernel<<<grid_for(dpad, 256), 256, 0, s>>>(rowptr, d, dpad, seg, nseg);
+    LRA_LAUNCHED();
+    exclusive_scan(s, nseg, dpad, item_off, scan_scratch);
+}
+
+void sparse_fill_items(cudaStream_t s, const int64_t *item_off, int64_t dpad, int2 *items) {
+    fill_items_kernel<<<grid_for(dpad, 256), 256, 0, s>>>(item_off, dpad, items);
+    LRA_LAUNCHED();
+}
+
+void sparse_colnorms(cudaStream_t s, const int64_t *colptr, const float *cval, int64_t n, double *norm2) {
+    sparse_colnorms_kernel<<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(colptr, cval, n, norm2);
+    LRA_LAUNCHED();
+}
+
+void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t n,
+             const float *Wr, int PP, float *Y) {
+    dispatch_nq(PP, [&](auto nq) {
+        constexpr int NQ = decltype(nq)::value;
+        spmm_xt_kernel<NQ><<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(colptr, rowidx, cval, n, Wr, PP, Y);
+        LRA_LAUNCHED();
+    });
+}
+
+void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+            int64_t dpad, const int64_t *item_off, const int2 *items, int64_t nitems, int seg, const float *Y,
+            int PP, float *G, float *partial) {
+    dispatch_nq(PP, [&](auto nq) {
+        constexpr int NQ = decltype(nq)::value;
+        spmm_x_kernel<NQ><<<grid_for(nitems, kWarps), 32 * kWarps, 0, s>>>(rowptr, colidx, val, d, item_off, items,
+                                                                          nitems, seg, Y, PP, G, partial);
+        LRA_LAUNCHED();
+    });
+    if (nitems > dpad) {
+        long_rows_kernel<<<grid_for(dpad, kWarps), 32 * kWarps, 0, s>>>(item_off, dpad, partial, PP, G);
+        LRA_LAUNCHED();
+    }
+}
+
+void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
+                    int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam) {
+    if (m <= 0) return;
+    zdiff_kernel<<<grid_for(dpad * PP, 256), 256, 0, s>>>(W, Wt, dpad, p, PP, Z);
+    LRA_LAUNCHED();
+    dispatch_nq(PP, [&](auto nq) {
+        constexpr int NQ = decltype(nq)::value;
+        inner_csc_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, eta, lam,
+                                                       ab);
+        LRA_LAUNCHED();
+    });
+    inner_final_kernel<<<grid_for(dpad * p, 256), 256, 0, s>>>(Wt, Z, Mr, ab, dpad, p, PP, W);
+    LRA_LAUNCHED();
+}
+
+}  // namespace lra

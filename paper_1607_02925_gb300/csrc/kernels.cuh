@@ -40,7 +40,7 @@ void pack_rm(cudaStream_t s, const float *W, int64_t ldw, int64_t rows, int p, i
 void xtw(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int64_t n,
          const float *Wr, int PP, float *Y);
 // partial G over column chunks: Gp[c] (dpad x PP row-major) = X[:, chunk c] Y[chunk c, :]
-int xy_chunks(int64_t dpad, int64_t n);
+int xy_chunks(int64_t dpad, int64_t n, int rows_per_cta = 128);
 void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int64_t n,
         const float *Y, int PP, float *Gp, int nchunks);
 // M = lambda Wt - sum_c Gp[c] - B (dpad x p column-major); if norms: norms[0] =
@@ -53,6 +53,9 @@ void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad,
 // ---- anchor pass on tensor cores, BF16 X (k_anchor_tc.cu) ---------------
 // leading dimension of the hi/lo BF16 copy of Y (n rounded up to 64)
 int64_t tc_ldy(int64_t n);
+// rows of X per CTA of the tensor-core passes (256 = two M tiles sharing the
+// small operand: BF16 X with PP >= 64; else 128)
+int tc_rows_per_cta(int PP, bool pair);
 // Wb = [hi; lo] BF16 split of W (rows x p column-major, leading dim ld), each
 // PP x rows column-major (zero for columns >= p)
 void pack_hilo(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, __nv_bfloat16 *Wb);
@@ -115,5 +118,37 @@ void col_dots(cudaStream_t s, const float *A, const float *B, int64_t rows, int6
 void scale_cols_rsqrt(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, const double *n2);
 // A = alpha * A (all rows x p)
 void scale_block(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, float alpha);
+
+// ---- sparse X (k_sparse.cu) -----------------------------------------------
+// Segment length of the row work list of X Y (rows longer than this are split).
+constexpr int kSparseSeg = 1024;
+// bad[0] |= 1 rowptr out of order/range, 2 column out of [0, n), 4 columns not
+// strictly increasing in a row, 8 value not finite, 16 rowptr[0]/rowptr[d] wrong
+void csr_check(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+               int64_t n, int64_t nnz, int *bad);
+// int64 scratch of an exclusive scan over N entries
+int64_t sparse_scan_scratch(int64_t N);
+// compressed columns (colptr[n+1], rowidx, cval) of a valid CSR, rows sorted
+// within each column; cnt: n int64, cursor: n int scratch
+void csr_transpose(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+                   int64_t n, int64_t nnz, int64_t *colptr, int32_t *rowidx, float *cval, int64_t *cnt,
+                   int *cursor, int64_t *scan_scratch);
+// item_off[dpad+1]: exclusive scan of the segment counts (nseg: dpad int64 scratch)
+void sparse_row_items(cudaStream_t s, const int64_t *rowptr, int64_t d, int64_t dpad, int seg, int64_t *nseg,
+                      int64_t *item_off, int64_t *scan_scratch);
+void sparse_fill_items(cudaStream_t s, const int64_t *item_off, int64_t dpad, int2 *items);
+void sparse_colnorms(cudaStream_t s, const int64_t *colptr, const float *cval, int64_t n, double *norm2);
+// Y (n x PP row-major) = X^T Wr (Wr dpad x PP row-major)
+void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t n,
+             const float *Wr, int PP, float *Y);
+// G (dpad x PP row-major) = X Y; partial >= nitems x PP floats
+void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
+            int64_t dpad, const int64_t *item_off, const int2 *items, int64_t nitems, int seg, const float *Y,
+            int PP, float *G, float *partial);
+// m inner steps in factored form: W (dpad x p col-major) from W = Wt + (W - Wt);
+// Mr = M packed dpad x PP row-major; Z: dpad x PP scratch; ab: 2 doubles
+void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
+                    int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam);
 
 }  // namespace lra

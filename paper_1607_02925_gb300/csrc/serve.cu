@@ -15,7 +15,7 @@ size_t job_footprint(const lra_mat *m, int k, int p, const Opts &o) {
     const int pmax = (o.shift_policy == LRA_SHIFT_PAPER && !(o.delta > 0)) ? p + 1 : p;
     const int64_t mcap = o.m_max > 0 ? o.m_max : 50 * m->n;
     const size_t idx = sizeof(int32_t) * 2 * (size_t)std::min<int64_t>(mcap, 4 * m->n + 4096);
-    return workspace_bytes(m->dpad, m->n, pmax) + idx + sizeof(float) * m->d * k + 64 * 1024;
+    return workspace_bytes(m->dpad, m->n, pmax, ws_items(m)) + idx + sizeof(float) * m->d * k + 64 * 1024;
 }
 
 int env_int(const char *name, int dflt) {
@@ -86,7 +86,8 @@ void Server::worker(int slot) {
         } else {
             try {
                 Workspace ws(ctx_, j->mat->dpad, j->mat->n,
-                             (j->opts.shift_policy == LRA_SHIFT_PAPER && !(j->opts.delta > 0)) ? j->p + 1 : j->p, s);
+                             (j->opts.shift_policy == LRA_SHIFT_PAPER && !(j->opts.delta > 0)) ? j->p + 1 : j->p, s,
+                             ws_items(j->mat));
                 j->U_bytes = sizeof(float) * j->mat->d * j->k;
                 j->ritz_bytes = sizeof(double) * j->k;
                 j->stream = s;

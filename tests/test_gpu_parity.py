@@ -78,7 +78,10 @@ def bf16_values(x32):
     return r.astype(np.uint32).view(np.float32)
 
 
-SHAPES = [(300, 3000, 13), (256, 2048, 10), (128, 777, 40), (520, 1500, 48)]
+# ragged d, n, p; p = 100 and 64 take the two-M-tile tensor-core kernels for BF16
+# X (d = 520 -> 5 row tiles of 128: the last CTA's second tile lies past dpad)
+SHAPES = [(300, 3000, 13), (256, 2048, 10), (128, 777, 40), (520, 1500, 48), (520, 1500, 100),
+          (1100, 3001, 64)]
 
 
 # ---------------------------------------------------------------------------
