@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-outer", type=int, default=4)
+    ap.add_argument("--max-outer", type=int, default=0, help="cap on outer iterations (0 = library default)")
     ap.add_argument("--serve", action="store_true", help="request-loop benchmark instead")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mean-ms", type=float, default=20.0)
@@ -61,6 +62,15 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The largest per-rank value (the job's time is its slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -376,6 +386,8 @@ def run_lra(args):
     delta = (lk - lp1) / 1.5
     pol = lra.LRA_SHIFT_FAR if args.shift == "far" else lra.LRA_SHIFT_PAPER
     opt = lra.options(shift_policy=pol, delta=delta, profile=1)
+    if args.max_outer > 0:
+        opt.max_outer = args.max_outer
 
     ctx = lra.lra_init(local)
     mat = src.create(ctx)
@@ -409,9 +421,7 @@ def run_lra(args):
     ms_total = e0.elapsed_time(e1)
     ms_step = ms_total / args.steps
     if world > 1:
-        t = torch.tensor([ms_step], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, device)
 
     # accuracy of the last solve, off the clock (FP64 error against the
     # closed-form or stored reference optimum)
