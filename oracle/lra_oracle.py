@@ -575,12 +575,16 @@ class Result:
     S: np.ndarray
 
 
-def outer_stop(E: list, eps: float, ell: int, min_outer: int) -> bool:
+def outer_stop(E: list, eps: float, ell: int, min_outer: int, r_floor: float = 0.0) -> bool:
     """Stop when the predicted remaining decrease of E is <= (eps/4) E_l.
 
-    With differences D_j = E_{j-1} - E_j, the rate is the geometric mean over
-    the last w <= 4 of them, r = clamp((D_l / D_{l-w})^(1/w), 0, .99) (r = .99
-    when D_{l-w} is not positive), and remaining = max(D_l, 0) r / (1 - r)."""
+    With differences D_j = E_{j-1} - E_j, the observed rate is the geometric
+    mean over the last w <= 4 of them, (D_l / D_{l-w})^(1/w) (R when D_{l-w} is
+    not positive), raised to at least r_floor, the rate Theorem 2 predicts for
+    the slowest direction; r is clamped to [0, R], R = 1 - 1e-6, and remaining
+    = max(D_l, 0) r / (1 - r).  Fast early components cannot end a slow
+    iteration, and a non-positive last difference (E at its rounding floor)
+    stops."""
     if ell + 1 < max(3, min_outer):
         return False
     w = min(4, len(E) - 2)
@@ -591,10 +595,25 @@ def outer_stop(E: list, eps: float, ell: int, min_outer: int) -> bool:
     elif d0 > 0:
         r = 0.0
     else:
-        r = 0.99
-    r = min(max(r, 0.0), 0.99)
+        r = RATE_MAX
+    r = min(max(r, r_floor, 0.0), RATE_MAX)
     remaining = max(d1, 0.0) * r / (1.0 - r)
     return remaining <= 0.25 * eps * E[-1]
+
+
+RATE_MAX = 1.0 - 1e-6
+
+
+def theory_rate(lam: float, rho: np.ndarray, k: int, p: int) -> float:
+    """Per-iteration decrease factor of E from Theorem 2 on D: tan theta_k
+    contracts by (lambda - lambda_k)/(lambda - lambda_{p+1}) per step and E's
+    excess by its square; estimated with the current Ritz values rho_k and
+    rho_p (rho_p <= lambda_p, which overestimates the factor once rho_p has
+    passed lambda_{p+1})."""
+    den = lam - float(rho[p - 1])
+    if den <= 0.0:
+        return RATE_MAX
+    return min(max((lam - float(rho[k - 1])) / den, 0.0), 1.0) ** 2
 
 
 def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options | None = None,
@@ -638,7 +657,7 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
         rho, Uh, Q, H = rayleigh_ritz(Xt, S)
         ctx.x_passes += 1
         E.append(ctx.fro2 - float(np.sum(rho[:k])))
-        if outer_stop(E, eps, ell, opts.min_outer):
+        if outer_stop(E, eps, ell, opts.min_outer, theory_rate(lam, rho, k, p)):
             break
         if ell >= opts.max_outer:
             status = "notconv"

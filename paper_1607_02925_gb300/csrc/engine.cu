@@ -297,7 +297,7 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
     if (mat_->sp) {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
         if (timer) timer->begin(KernelTimer::XTW, p);
-        spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, ws_.Wr, PP, Y);
+        spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, ws_.Wr, PP, p, Y);
         if (timer) timer->end();
     } else if (tc(use32)) {
         pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
@@ -321,7 +321,7 @@ void Engine::xy_pass(const float *Y32, int p, bool use32) {
         ws_.nch = 1;
         if (timer) timer->begin(KernelTimer::XY, p);
         spmm_x(s_, sp.rowptr, sp.colidx, sp.val, mat_->d, mat_->dpad, sp.item_off, sp.items, sp.nitems, kSparseSeg,
-               Y32, PP, ws_.Gp, ws_.partial);
+               Y32, PP, p, ws_.Gp, ws_.partial);
         if (timer) timer->end();
     } else if (tc(use32)) {
         if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
@@ -599,9 +599,22 @@ static double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Stop rule of the outer loop: predicted remaining decrease of E_l
-// (r = clamp((E_{l-1}-E_l)/(E_{l-2}-E_{l-1}), 0, .99)) at most (eps/4) E_l.
-static bool outer_stop(const std::vector<double> &E, double eps, int ell, int min_outer) {
+// Stop rule of the outer loop: the predicted remaining decrease of E_l is at
+// most (eps/4) E_l, remaining = max(D_l, 0) r / (1 - r) with D_j = E_{j-1} - E_j
+// and r the geometric-mean rate of the last w <= 4 differences (the upper clamp
+// when D_{l-w} <= 0), at least r_floor, clamped to [0, 1 - 1e-6].
+constexpr double kRateMax = 1.0 - 1e-6;
+
+// Theorem 2's per-iteration factor of E's excess, ((lambda - rho_k)/(lambda - rho_p))^2,
+// from the current Ritz values (a floor for the observed rate).
+static double theory_rate(double lam, const double *rho, int k, int p) {
+    const double den = lam - rho[p - 1];
+    if (den <= 0.0) return kRateMax;
+    const double f = std::min(std::max((lam - rho[k - 1]) / den, 0.0), 1.0);
+    return f * f;
+}
+
+static bool outer_stop(const std::vector<double> &E, double eps, int ell, int min_outer, double r_floor) {
     if (ell + 1 < std::max(3, min_outer)) return false;
     const size_t n = E.size();
     const size_t w = std::min<size_t>(4, n - 2);
@@ -613,8 +626,8 @@ static bool outer_stop(const std::vector<double> &E, double eps, int ell, int mi
     else if (d0 > 0)
         r = 0.0;
     else
-        r = 0.99;
-    r = std::min(std::max(r, 0.0), 0.99);
+        r = kRateMax;
+    r = std::min(std::max(std::max(r, r_floor), 0.0), kRateMax);
     const double remaining = std::max(d1, 0.0) * r / (1.0 - r);
     return remaining <= 0.25 * eps * E[n - 1];
 }
@@ -689,7 +702,7 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
         for (int j = 0; j < k; ++j) sk += h[j];
         E.push_back(mat_->fro2 - sk);
         if (o.trace_E && (int)E.size() <= o.trace_cap) o.trace_E[E.size() - 1] = E.back();
-        if (outer_stop(E, eps, ell, o.min_outer)) break;
+        if (outer_stop(E, eps, ell, o.min_outer, theory_rate(lam, h, k, p))) break;
         if (ell >= o.max_outer) {
             status = LRA_ENOTCONV;
             break;

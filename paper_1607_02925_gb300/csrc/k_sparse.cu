@@ -293,28 +293,56 @@ __global__ void sparse_colnorms_kernel(const int64_t *__restrict__ colptr, const
 }
 
 // ---------------------------------------------------------------------------
-// Gather-accumulate of one compressed line: acc[q] += v_k * B[idx_k * PP + lane + 32 q]
-// over k in [lo, hi), entries broadcast from lane-cooperative loads.
+// Gather-accumulate of one compressed line: acc = sum over k in [lo, hi) of
+// v_k * B[idx_k, :] (B row-major, PP wide).  The two half-warps take
+// alternate entries; lane l of a half holds columns 2l, 2l + 1 (+ 32 q) as a
+// float2 and loads only columns below p (the padding columns of B are zero).
+// On return both halves hold the whole sum (halves added in a fixed order).
 // ---------------------------------------------------------------------------
 template <int NQ>
 __device__ __forceinline__ void gather_line(const int32_t *__restrict__ idx, const float *__restrict__ vals,
-                                            int64_t lo, int64_t hi, const float *__restrict__ B, int PP,
-                                            int lane, float (&acc)[NQ]) {
+                                            int64_t lo, int64_t hi, const float *__restrict__ B, int PP, int p,
+                                            int lane, float2 (&acc)[NQ]) {
+    const int h = lane >> 4, l = lane & 15;
     for (int64_t base = lo; base < hi; base += 32) {
         const int64_t k = base + lane;
         const int32_t rr = k < hi ? idx[k] : 0;
         const float vv = k < hi ? vals[k] : 0.0f;
         const int cnt = (int)((hi - base) < 32 ? (hi - base) : 32);
 #pragma unroll 4
-        for (int e = 0; e < cnt; ++e) {
-            const int64_t r = __shfl_sync(0xffffffffu, rr, e);
-            const float v = __shfl_sync(0xffffffffu, vv, e);
-            const float *row = B + r * PP;
+        for (int e = 0; e < cnt; e += 2) {
+            const int src = e + h;
+            const int64_t r = __shfl_sync(0xffffffffu, rr, src);
+            const float v = __shfl_sync(0xffffffffu, vv, src);
+            if (src < cnt) {
+                const float *row = B + r * PP;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int j = lane + 32 * q;
-                if (j < PP) acc[q] = fmaf(v, __ldg(row + j), acc[q]);
+                for (int q = 0; q < NQ; ++q) {
+                    const int j = 2 * l + 32 * q;
+                    if (j < p) {
+                        const float2 b = __ldg(reinterpret_cast<const float2 *>(row + j));
+                        acc[q].x = fmaf(v, b.x, acc[q].x);
+                        acc[q].y = fmaf(v, b.y, acc[q].y);
+                    }
+                }
             }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, 16);
+        acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, 16);
+    }
+}
+
+// half-warp 0 stores a PP-wide row (float2 per lane)
+template <int NQ>
+__device__ __forceinline__ void store_line(float *__restrict__ dst, int PP, int lane, const float2 (&acc)[NQ]) {
+    if (lane < 16) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = 2 * lane + 32 * q;
+            if (j < PP) *reinterpret_cast<float2 *>(dst + j) = acc[q];
         }
     }
 }
@@ -324,19 +352,15 @@ template <int NQ>
 __global__ void __launch_bounds__(32 * kWarps) spmm_xt_kernel(const int64_t *__restrict__ colptr,
                                                               const int32_t *__restrict__ rowidx,
                                                               const float *__restrict__ cval, int64_t n,
-                                                              const float *__restrict__ Wr, int PP,
+                                                              const float *__restrict__ Wr, int PP, int p,
                                                               float *__restrict__ Y) {
     const int lane = threadIdx.x & 31;
     for (int64_t i = global_warp(); i < n; i += warps_in_grid()) {
-        float acc[NQ];
+        float2 acc[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
-        gather_line<NQ>(rowidx, cval, colptr[i], colptr[i + 1], Wr, PP, lane, acc);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int j = lane + 32 * q;
-            if (j < PP) Y[i * PP + j] = acc[q];
-        }
+        for (int q = 0; q < NQ; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        gather_line<NQ>(rowidx, cval, colptr[i], colptr[i + 1], Wr, PP, p, lane, acc);
+        store_line<NQ>(Y + i * PP, PP, lane, acc);
     }
 }
 
@@ -348,7 +372,7 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_x_kernel(const int64_t *__re
                                                              const float *__restrict__ val, int64_t d,
                                                              const int64_t *__restrict__ item_off,
                                                              const int2 *__restrict__ items, int64_t nitems,
-                                                             int seg, const float *__restrict__ Y, int PP,
+                                                             int seg, const float *__restrict__ Y, int PP, int p,
                                                              float *__restrict__ G, float *__restrict__ partial) {
     const int lane = threadIdx.x & 31;
     for (int64_t it = global_warp(); it < nitems; it += warps_in_grid()) {
@@ -360,17 +384,12 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_x_kernel(const int64_t *__re
             hi = rowptr[r + 1];
             if (hi > lo + seg) hi = lo + seg;
         }
-        float acc[NQ];
+        float2 acc[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
-        gather_line<NQ>(colidx, val, lo, hi, Y, PP, lane, acc);
+        for (int q = 0; q < NQ; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        gather_line<NQ>(colidx, val, lo, hi, Y, PP, p, lane, acc);
         const bool single = (item_off[r + 1] - item_off[r]) == 1;
-        float *dst = single ? G + r * PP : partial + it * PP;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int j = lane + 32 * q;
-            if (j < PP) dst[j] = acc[q];
-        }
+        store_line<NQ>(single ? G + r * PP : partial + it * PP, PP, lane, acc);
     }
 }
 
@@ -557,21 +576,21 @@ void sparse_colnorms(cudaStream_t s, const int64_t *colptr, const float *cval, i
 }
 
 void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t n,
-             const float *Wr, int PP, float *Y) {
+             const float *Wr, int PP, int p, float *Y) {
     dispatch_nq(PP, [&](auto nq) {
         constexpr int NQ = decltype(nq)::value;
-        spmm_xt_kernel<NQ><<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(colptr, rowidx, cval, n, Wr, PP, Y);
+        spmm_xt_kernel<NQ><<<grid_for(n, kWarps), 32 * kWarps, 0, s>>>(colptr, rowidx, cval, n, Wr, PP, p, Y);
         LRA_LAUNCHED();
     });
 }
 
 void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
             int64_t dpad, const int64_t *item_off, const int2 *items, int64_t nitems, int seg, const float *Y,
-            int PP, float *G, float *partial) {
+            int PP, int p, float *G, float *partial) {
     dispatch_nq(PP, [&](auto nq) {
         constexpr int NQ = decltype(nq)::value;
         spmm_x_kernel<NQ><<<grid_for(nitems, kWarps), 32 * kWarps, 0, s>>>(rowptr, colidx, val, d, item_off, items,
-                                                                          nitems, seg, Y, PP, G, partial);
+                                                                          nitems, seg, Y, PP, p, G, partial);
         LRA_LAUNCHED();
     });
     if (nitems > dpad) {
