@@ -532,6 +532,9 @@ def run_lra(args):
             "gpu_launches": int(sum(r.kernel_launches for _, r in reps)),
             "kernel_ms": {k: v / args.steps for k, v in tot.items()},
             "kernels": per_kernel,
+            "phases_ms": {name: sum(r.phase_ms[i] for _, r in reps) / args.steps
+                          for i, name in enumerate(["xtw", "xy", "inner", "ritz_gram", "eig", "cholqr2",
+                                                    "warm_start", "epilogue"])},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -120,6 +120,11 @@ typedef struct lra_report {
     int64_t xtw_launches, xy_launches, inner_launches;
     int64_t xtw_cols;       /* total columns (p) processed by the X^T W launches */
     int64_t xy_cols;        /* total columns (p) processed by the X Y launches */
+    /* with options.profile = 1: device time per phase of the solve, ms:
+     * [0] X^T W, [1] X Y, [2] inner loop (as above), [3] Rayleigh-Ritz Gram
+     * matrices and their correction, [4] eigensolver, [5] CholeskyQR2,
+     * [6] basis rotation and warm start, [7] anchor epilogue and sampling */
+    double phase_ms[8];
 } lra_report;
 
 /* ---------------------------------------------------------------------------

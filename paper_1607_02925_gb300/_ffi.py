@@ -89,6 +89,7 @@ class LraReport(C.Structure):
         ("inner_launches", C.c_int64),
         ("xtw_cols", C.c_int64),
         ("xy_cols", C.c_int64),
+        ("phase_ms", C.c_double * 8),
     ]
 
     def __init__(self):

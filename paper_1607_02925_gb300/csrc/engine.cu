@@ -145,6 +145,8 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
             Yb = alloc<__nv_bfloat16>((size_t)2 * PPmax * ldy);
         }
         LRA_CUDA(cudaMallocHost(&host, sizeof(double) * (2 * pmax + 16)));
+        LRA_CUDA(cudaMallocHost(&hstat, sizeof(int) * 4));
+        hstat[0] = hstat[1] = 0;
     } catch (...) {
         for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
         allocs.clear();
@@ -159,6 +161,7 @@ Workspace::~Workspace() {
     if (cval) dev_free(ctx, cval, sizeof(float) * idx_cap, astream);
     if (astream) cudaStreamSynchronize(astream);
     if (host) cudaFreeHost(host);
+    if (hstat) cudaFreeHost(hstat);
 }
 
 void Workspace::ensure_idx(int64_t m) {
@@ -205,9 +208,9 @@ void KernelTimer::end() {
     recs_.back().e1 = b;
 }
 
-void KernelTimer::collect(double ms[3], int64_t launches[3], int64_t cols[3]) {
+void KernelTimer::collect(double ms[NKIND], int64_t launches[NKIND], int64_t cols[NKIND]) {
     LRA_CUDA(cudaStreamSynchronize(s_));
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < NKIND; ++i) {
         ms[i] = 0.0;
         launches[i] = 0;
         cols[i] = 0;
@@ -292,7 +295,7 @@ void Engine::check_tc() {
     }
 }
 
-void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
+void Engine::xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo) {
     const int PP = pad_p(p);
     if (mat_->sp) {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
@@ -302,7 +305,9 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32) {
     } else if (tc(use32)) {
         pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
         if (timer) timer->begin(KernelTimer::XTW, p);
-        xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, ws_.Yb,
+        // the BF16 hi/lo copy of Y feeds a following X Y pass; an FP32 result
+        // (Rayleigh-Ritz, the power steps) is used alone unless keep_hilo
+        xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, (Y && !keep_hilo) ? nullptr : ws_.Yb,
                ws_.ldy, ws_.tcerr);
         if (timer) timer->end();
     } else {
@@ -356,11 +361,14 @@ void Engine::a_apply(const float *W, int p, float *G) {
                     ws_.epi);
 }
 
-void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *Y0,
+void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
                     double *nM2, double *nB2) {
     const int PP = pad_p(p);
-    if (Y0) {
-        xy_pass(Y0, p, false);
+    const float *Gsrc = ws_.Gp;
+    int nch = 0;
+    if (G0) {
+        Gsrc = G0;  // X X^T Wt supplied by the caller (one dpad x PP chunk)
+        nch = 1;
     } else if (tc(false)) {
         xt_mul(Wt, p, nullptr, false);
         xy_pass(nullptr, p, false);
@@ -368,7 +376,10 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
         xt_mul(Wt, p, ws_.Y, false);
         xy_pass(ws_.Y, p, false);
     }
-    anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
+    if (!G0) nch = ws_.nch;
+    if (timer) timer->begin(KernelTimer::EPI, p);
+    anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
+    if (timer) timer->end();
     if (nM2 || nB2) {
         LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
         if (tc(false)) check_tc();
@@ -397,8 +408,9 @@ void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32
     if (timer) timer->end();
 }
 
-lra_status Engine::cholqr2(float *W, int p) {
+lra_status Engine::cholqr2(float *W, int p, bool deferred) {
     const int64_t dpad = mat_->dpad;
+    if (timer) timer->begin(KernelTimer::QR, p);
     LRA_CUDA(cudaMemsetAsync(ws_.status, 0, sizeof(int) * 2, s_));
     for (int pass = 0; pass < 2; ++pass) {
         gram(s_, W, dpad, 1, dpad, p, ws_.Gm, ws_.gscr);
@@ -406,19 +418,25 @@ lra_status Engine::cholqr2(float *W, int p) {
         trsm_rows(s_, W, dpad, dpad, p, ws_.Rinv, ws_.T1);
         LRA_CUDA(cudaMemcpyAsync(W, ws_.T1, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
     }
-    int st[2];
-    LRA_CUDA(cudaMemcpyAsync(st, ws_.status, sizeof(st), cudaMemcpyDeviceToHost, s_));
+    if (timer) timer->end();
+    LRA_CUDA(cudaMemcpyAsync(ws_.hstat, ws_.status, sizeof(int) * 2, cudaMemcpyDeviceToHost, s_));
+    if (deferred) return LRA_OK;  // the caller reads the flags after its next synchronisation
     sync();
-    if (st[0] || st[1]) {
+    return qr_status();
+}
+
+lra_status Engine::qr_status() const {
+    if (ws_.hstat[0] || ws_.hstat[1]) {
         set_error("CholeskyQR2: Gram matrix not positive definite");
         return LRA_ENUMERIC;
     }
     return LRA_OK;
 }
 
-void Engine::ritz(const float *S, int p, bool use32, int passes) {
+void Engine::ritz(const float *S, int p, bool use32, int passes, bool keep_hilo) {
     const int PP = pad_p(p);
-    xt_mul(S, p, ws_.Q, use32);
+    xt_mul(S, p, ws_.Q, use32, keep_hilo);
+    if (timer) timer->begin(KernelTimer::RITZ, p);
     gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
     // S is orthonormal to FP32 rounding only; correct H to first order in
     // S^T S - I, with the Gram of the basis the X pass actually used.
@@ -427,7 +445,10 @@ void Engine::ritz(const float *S, int p, bool use32, int passes) {
     else
         gram64(s_, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr);
     ortho_correct(s_, ws_.H, ws_.Gm, p, ws_.Hc);
+    if (timer) timer->end();
+    if (timer) timer->begin(KernelTimer::EIG, p);
     sym_eig(s_, ws_.Hc, p, ws_.evals, ws_.evecs, ws_.eigwork, passes);
+    if (timer) timer->end();
 }
 
 void Engine::normalize(float *z) {
@@ -451,7 +472,7 @@ void Engine::step_params(double lam, double mu, double l1up, double kappa, const
 }
 
 lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
-                              uint64_t seed, int64_t solve_id, const Opts &o, const float *Y0,
+                              uint64_t seed, int64_t solve_id, const Opts &o, const float *G0,
                               SolveInfo &info) {
     const auto &tab = ensure_table(o.sampling);
     double eta;
@@ -467,7 +488,7 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
     for (int e = 0; e < max_e; ++e) {
         LRA_CUDA(cudaMemcpyAsync(ws_.Wt, W, blk, cudaMemcpyDeviceToDevice, s_));
         double nM2, nB2;
-        anchor(ws_.Wt, B, p, lam, ws_.M, (e == 0) ? Y0 : nullptr, &nM2, &nB2);
+        anchor(ws_.Wt, B, p, lam, ws_.M, (e == 0) ? G0 : nullptr, &nM2, &nB2);
         stats.epochs += 1;
         const double res = nB2 > 0 ? std::sqrt(nM2 / nB2) : 0.0;
         info.epochs = e + 1;
@@ -695,9 +716,10 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     const int PP = pad_p(p);
     double *h = ws_.host;
     while (true) {
-        ritz(S, p, false, 1);
+        ritz(S, p, false, 1, o.warm_start != 0);
         LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
         sync();
+        if (ell > 0 && (st = qr_status()) != LRA_OK) return st;  // the previous step's CholeskyQR2
         double sk = 0.0;
         for (int j = 0; j < k; ++j) sk += h[j];
         E.push_back(mat_->fro2 - sk);
@@ -708,24 +730,35 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
             break;
         }
         if (cancel && cancel->load()) return LRA_ECANCELLED;
-        const float *Y0 = nullptr;
+        const float *G0 = nullptr;
         if (o.warm_start) {
-            ritz_inverse(s_, ws_.evecs, ws_.evals, p, lam, ws_.P);
+            // Move the basis onto the Ritz vectors, S <- S V (same span, so the
+            // same Algorithm 1 step; the next Rayleigh-Ritz matrix is then
+            // nearly diagonal and the eigensolver's sweeps stop early).  Warm
+            // start in that basis: W0 = S V diag(1/(lam - rho)); the first
+            // anchor's X X^T W0 = (X Q) V diag(1/(lam - rho)) with Q = X^T S from
+            // the Rayleigh-Ritz pass: one X Y pass and a d x p product.
+            x_mul(tc(false) ? nullptr : ws_.Q, p, ws_.T1, false);
+            if (timer) timer->begin(KernelTimer::WARM, p);
+            evecs_to_rm(s_, ws_.evecs, p, p, ws_.P);
             apply_right(s_, S, dpad, 1, dpad, p, ws_.P, p, W, 1, dpad);
-            apply_right(s_, ws_.Q, mat_->n, PP, 1, p, ws_.P, p, ws_.Y, PP, 1);
-            Y0 = ws_.Y;
+            LRA_CUDA(cudaMemcpyAsync(S, W, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
+            shift_scale_cols(s_, S, W, dpad, dpad, p, ws_.evals, lam);
+            ritz_scaled(s_, ws_.evecs, ws_.evals, p, lam, ws_.P);
+            apply_right(s_, ws_.T1, dpad, 1, dpad, p, ws_.P, p, ws_.Gp, PP, 1);
+            if (timer) timer->end();
+            G0 = ws_.Gp;
         } else {
             LRA_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * dpad * p, s_));
         }
         SolveInfo info;
-        st = svrg_solve(S, W, p, lam, mu, l1up, seed, solve_count++, o, Y0, info);
+        st = svrg_solve(S, W, p, lam, mu, l1up, seed, solve_count++, o, G0, info);
         if (st != LRA_OK) return st;
         R.eta = info.eta;
         R.m = info.m;
         R.last_residual = info.residual;
         std::swap(S, W);
-        st = cholqr2(S, p);
-        if (st != LRA_OK) return st;
+        cholqr2(S, p, true);
         ++ell;
     }
     R.outer_iters = ell;
@@ -758,9 +791,10 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     R.status = status;
     R.kernel_launches = launches_of_thread() - launches0;
     if (timer) {
-        double ms[3];
-        int64_t cnt[3], cols[3];
+        double ms[KernelTimer::NKIND];
+        int64_t cnt[KernelTimer::NKIND], cols[KernelTimer::NKIND];
         timer->collect(ms, cnt, cols);
+        for (int i = 0; i < KernelTimer::NKIND; ++i) R.phase_ms[i] = ms[i];
         R.xtw_ms = ms[0];
         R.xy_ms = ms[1];
         R.inner_ms = ms[2];

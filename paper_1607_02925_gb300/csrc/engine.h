@@ -85,13 +85,13 @@ struct Opts {
 // CUDA-event timing of individual kernel launches on the engine's stream.
 class KernelTimer {
    public:
-    enum Kind { XTW = 0, XY = 1, INNER = 2 };
+    enum Kind { XTW = 0, XY = 1, INNER = 2, RITZ = 3, EIG = 4, QR = 5, WARM = 6, EPI = 7, NKIND = 8 };
     explicit KernelTimer(cudaStream_t s) : s_(s) {}
     ~KernelTimer();
     void begin(Kind k, int cols);
     void end();
     // summed milliseconds, launch counts and processed columns per kind
-    void collect(double ms[3], int64_t launches[3], int64_t cols[3]);
+    void collect(double ms[NKIND], int64_t launches[NKIND], int64_t cols[NKIND]);
 
    private:
     size_t event();
@@ -139,6 +139,7 @@ struct Workspace {
     float *cval = nullptr;
     int64_t idx_cap = 0;
     double *host = nullptr;  // pinned readback area
+    int *hstat = nullptr;    // pinned CholeskyQR2 status flags
     std::vector<std::pair<void *, size_t>> allocs;
 
     // astream != nullptr: buffers come from the stream-ordered allocator on that
@@ -176,23 +177,28 @@ class Engine {
     const lra_mat::Table &ensure_table(int mode);
 
     // X products on p columns (internal padded layouts)
-    void xt_mul(const float *W, int p, float *Y, bool use32);            // Y n x PP rm
+    // Y n x PP rm; keep_hilo: also leave Y's BF16 hi/lo copy for a following X Y pass
+    void xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo = false);
     void x_mul(const float *Y, int p, float *G, bool use32);             // G dpad x p
     void a_apply(const float *W, int p, float *G);                       // G = X X^T W
-    void anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *Y0,
+    // G0 != nullptr: X X^T Wt precomputed (dpad x PP row-major), no X pass
+    void anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
                 double *nM2, double *nB2);
     void inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
                const float *cval, int64_t m, double eta, double lam);
-    lra_status cholqr2(float *W, int p);
+    // deferred: enqueue the status read-back without waiting (check with qr_status()
+    // after the next synchronisation of the stream)
+    lra_status cholqr2(float *W, int p, bool deferred = false);
+    lra_status qr_status() const;
     // -> ws.Q, ws.H, ws.evals, ws.evecs; passes = FP64 refinement passes of the eigensolver
-    void ritz(const float *S, int p, bool use32, int passes = 2);
+    void ritz(const float *S, int p, bool use32, int passes = 2, bool keep_hilo = false);
     void normalize(float *z);                      // one column, in place
     double dot1(const float *a, const float *b);   // host read
 
     void step_params(double lam, double mu, double l1up, double kappa, const Opts &o, double &eta,
                      int64_t &m) const;
     lra_status svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
-                          uint64_t seed, int64_t solve_id, const Opts &o, const float *Y0,
+                          uint64_t seed, int64_t solve_id, const Opts &o, const float *G0,
                           SolveInfo &info);
     double lambda1_estimate(uint64_t seed);
     lra_status d_top_inverse(uint64_t seed, int rnd, double lam, double mu, double l1up,

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
     if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
     } else {
-#pragma unroll
+#pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
         const int64_t i = i0 + mt * kBM + warp * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + mt * kAccCols;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
     if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
     } else {
-#pragma unroll
+#pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
         const int64_t r = r0 + mt * kBM + warp * 32 + lane;
         float *out = Gp + (int64_t)blockIdx.y * dpad * PP + r * PP;

@@ -569,6 +569,26 @@ __global__ void ritz_inverse_kernel(const double *__restrict__ V, const double *
     }
 }
 
+// P (p x p FP32 row-major) = V diag(1/(lam - rho)): the Galerkin inverse
+// (lam I - H)^-1 expressed from the Ritz basis S V
+__global__ void ritz_scaled_kernel(const double *__restrict__ V, const double *__restrict__ rho, int p,
+                                   double lam, float *__restrict__ P) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p * p) return;
+    const int a = e / p, j = e % p;
+    P[e] = (float)(V[a + (int64_t)j * p] / (lam - rho[j]));
+}
+
+// dst[:, j] = src[:, j] / (lam - rho[j])
+__global__ void shift_scale_cols_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t rows,
+                                        int64_t ld, int p, const double *__restrict__ rho, double lam) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * p;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / rows, r = e - j * rows;
+        dst[r + j * ld] = (float)((double)src[r + j * ld] / (lam - rho[j]));
+    }
+}
+
 __global__ void evecs_to_rm_kernel(const double *__restrict__ V, int p, int k, float *__restrict__ T) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= p * k) return;
@@ -722,6 +742,18 @@ int64_t sym_eig_work(int p) { return (int64_t)3 * p * p + p; }
 
 void ritz_inverse(cudaStream_t s, const double *evecs, const double *evals, int p, double lam, float *P) {
     ritz_inverse_kernel<<<p, 128, 0, s>>>(evecs, evals, p, lam, P);
+    LRA_LAUNCHED();
+}
+
+void ritz_scaled(cudaStream_t s, const double *evecs, const double *evals, int p, double lam, float *P) {
+    ritz_scaled_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(evecs, evals, p, lam, P);
+    LRA_LAUNCHED();
+}
+
+void shift_scale_cols(cudaStream_t s, const float *src, float *dst, int64_t rows, int64_t ld, int p,
+                      const double *evals, double lam) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(rows * p, 256), 152 * 16);
+    shift_scale_cols_kernel<<<blocks, 256, 0, s>>>(src, dst, rows, ld, p, evals, lam);
     LRA_LAUNCHED();
 }
 

@@ -427,6 +427,8 @@ __global__ void zdiff_kernel(const float *__restrict__ W, const float *__restric
     }
 }
 
+constexpr int kColCap = 1024;  // entries of a column staged in shared memory (longer: read in place)
+
 template <int NQ>
 __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *__restrict__ colptr,
                                                                 const int32_t *__restrict__ rowidx,
@@ -435,20 +437,56 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
                                                                 const int32_t *__restrict__ idx,
                                                                 const float *__restrict__ cvals, int64_t m, double eta,
                                                                 double lam, double *__restrict__ ab) {
+    constexpr int kPer = kColCap / (32 * kWarps);  // staged entries per thread
+    __shared__ int32_t sr[2][kColCap];
+    __shared__ float sv[2][kColCap];
     __shared__ float redz[kWarps][32 * NQ], redm[kWarps][32 * NQ];
     __shared__ float rv[32 * NQ];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const double g = 1.0 - eta * lam;
     double a = 1.0, b = 0.0;
+
+    // column of step 0 into buffer 0
+    int64_t lo = colptr[idx[0]], hi = colptr[idx[0] + 1];
+    if (hi - lo <= kColCap) {
+        for (int64_t e = tid; e < hi - lo; e += blockDim.x) {
+            sr[0][e] = rowidx[lo + e];
+            sv[0][e] = cval[lo + e];
+        }
+    }
+    __syncthreads();
     for (int64_t t = 0; t < m; ++t) {
-        const int64_t i = idx[t];
-        const int64_t lo = colptr[i], hi = colptr[i + 1];
+        const int cur = (int)(t & 1);
+        const int64_t len = hi - lo;
+        const bool staged = len <= kColCap;
+        const int32_t *er = staged ? sr[cur] : rowidx + lo;
+        const float *ev = staged ? sv[cur] : cval + lo;
+
+        // next step's column: its bounds and entries travel while this step runs
+        int64_t lo1 = 0, hi1 = 0;
+        int32_t pr[kPer];
+        float pv[kPer];
+        if (t + 1 < m) {
+            const int64_t i1 = idx[t + 1];
+            lo1 = colptr[i1];
+            hi1 = colptr[i1 + 1];
+            if (hi1 - lo1 <= kColCap) {
+#pragma unroll
+                for (int u = 0; u < kPer; ++u) {
+                    const int64_t e = tid + (int64_t)u * blockDim.x;
+                    pr[u] = e < hi1 - lo1 ? rowidx[lo1 + e] : 0;
+                    pv[u] = e < hi1 - lo1 ? cval[lo1 + e] : 0.0f;
+                }
+            }
+        }
+
         float sz[NQ], sm[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) sz[q] = sm[q] = 0.0f;
-        for (int64_t k = lo + w; k < hi; k += kWarps) {
-            const int64_t r = rowidx[k];
-            const float v = cval[k];
+#pragma unroll 4
+        for (int64_t e = w; e < len; e += kWarps) {
+            const int64_t r = er[e];
+            const float v = ev[e];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int j = lane + 32 * q;
@@ -464,38 +502,52 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
             redm[w][lane + 32 * q] = sm[q];
         }
         __syncthreads();
-        if (threadIdx.x < 32 * NQ) {
+        if (tid < 32 * NQ) {
             float z = 0.0f, mm = 0.0f;
 #pragma unroll
             for (int u = 0; u < kWarps; ++u) {
-                z += redz[u][threadIdx.x];
-                mm += redm[u][threadIdx.x];
+                z += redz[u][tid];
+                mm += redm[u][tid];
             }
-            rv[threadIdx.x] = (float)(a * (double)z + b * (double)mm);
+            rv[tid] = (float)(a * (double)z + b * (double)mm);
         }
         __syncthreads();
         const double a1 = g * a;
         b = g * b - eta;
         const float coef = (float)(eta * (double)cvals[t] / a1);
-        for (int64_t k = lo + w; k < hi; k += kWarps) {
-            const int64_t r = rowidx[k];
-            const float cv = coef * cval[k];
+#pragma unroll 4
+        for (int64_t e = w; e < len; e += kWarps) {
+            const int64_t r = er[e];
+            const float cv = coef * ev[e];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int j = lane + 32 * q;
                 if (j < PP) Z[r * PP + j] = fmaf(cv, rv[j], Z[r * PP + j]);
             }
         }
+        // stage the next column (the other buffer is no longer read)
+        if (t + 1 < m && hi1 - lo1 <= kColCap) {
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int64_t e = tid + (int64_t)u * blockDim.x;
+                if (e < hi1 - lo1) {
+                    sr[cur ^ 1][e] = pr[u];
+                    sv[cur ^ 1][e] = pv[u];
+                }
+            }
+        }
         a = a1;
         if (a < 0x1p-30) {
             __syncthreads();
             const float af = (float)a;
-            for (int64_t e = threadIdx.x; e < dpad * PP; e += blockDim.x) Z[e] *= af;
+            for (int64_t e = tid; e < dpad * PP; e += blockDim.x) Z[e] *= af;
             a = 1.0;
         }
+        lo = lo1;
+        hi = hi1;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         ab[0] = a;
         ab[1] = b;
     }

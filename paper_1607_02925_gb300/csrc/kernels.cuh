@@ -109,6 +109,11 @@ void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evec
 // the Galerkin inverse (lam I - H)^-1 on the Ritz basis.  kcols = p.
 void ritz_inverse(cudaStream_t s, const double *evecs, const double *evals, int p, double lam,
                   float *P);
+// P (p x p FP32 row-major) = V diag(1/(lam - rho))
+void ritz_scaled(cudaStream_t s, const double *evecs, const double *evals, int p, double lam, float *P);
+// dst[:, j] = src[:, j] / (lam - rho[j]) (rows x p column-major, leading dim ld)
+void shift_scale_cols(cudaStream_t s, const float *src, float *dst, int64_t rows, int64_t ld, int p,
+                      const double *evals, double lam);
 // T (p x k FP32 row-major) = first k columns of evecs
 void evecs_to_rm(cudaStream_t s, const double *evecs, int p, int k, float *T);
 // out[j] = sum_r A[r, j] B[r, j] (FP64) for j < p (column-major, leading dim ld)
