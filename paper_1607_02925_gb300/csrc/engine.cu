@@ -433,11 +433,23 @@ lra_status Engine::qr_status() const {
     return LRA_OK;
 }
 
-void Engine::ritz(const float *S, int p, bool use32, int passes, bool keep_hilo) {
+void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
     const int PP = pad_p(p);
-    xt_mul(S, p, ws_.Q, use32, keep_hilo);
-    if (timer) timer->begin(KernelTimer::RITZ, p);
-    gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
+    xt_mul(S, p, ws_.Q, use32, with_xq);
+    if (with_xq) {
+        // X Q (kept in T1 for the warm start) and H = S^T (X Q): the Ritz
+        // matrix from a d-long contraction instead of the n-long Q^T Q
+        x_mul(tc(use32) ? nullptr : ws_.Q, p, ws_.T1, use32);
+        if (timer) timer->begin(KernelTimer::RITZ, p);
+        if (tc(use32))
+            cross_gram(s_, nullptr, ws_.Wb, ws_.Wb + (size_t)PP * mat_->dpad, ws_.T1, mat_->dpad, mat_->dpad, p,
+                       ws_.H, ws_.gscr);
+        else
+            cross_gram(s_, S, nullptr, nullptr, ws_.T1, mat_->dpad, mat_->dpad, p, ws_.H, ws_.gscr);
+    } else {
+        if (timer) timer->begin(KernelTimer::RITZ, p);
+        gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
+    }
     // S is orthonormal to FP32 rounding only; correct H to first order in
     // S^T S - I, with the Gram of the basis the X pass actually used.
     if (tc(use32))
@@ -736,9 +748,8 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
             // same Algorithm 1 step; the next Rayleigh-Ritz matrix is then
             // nearly diagonal and the eigensolver's sweeps stop early).  Warm
             // start in that basis: W0 = S V diag(1/(lam - rho)); the first
-            // anchor's X X^T W0 = (X Q) V diag(1/(lam - rho)) with Q = X^T S from
-            // the Rayleigh-Ritz pass: one X Y pass and a d x p product.
-            x_mul(tc(false) ? nullptr : ws_.Q, p, ws_.T1, false);
+            // anchor's X X^T W0 = (X Q) V diag(1/(lam - rho)) with X Q from the
+            // Rayleigh-Ritz step: a d x p product.
             if (timer) timer->begin(KernelTimer::WARM, p);
             evecs_to_rm(s_, ws_.evecs, p, p, ws_.P);
             apply_right(s_, S, dpad, 1, dpad, p, ws_.P, p, W, 1, dpad);

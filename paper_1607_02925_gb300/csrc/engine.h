@@ -191,7 +191,8 @@ class Engine {
     lra_status cholqr2(float *W, int p, bool deferred = false);
     lra_status qr_status() const;
     // -> ws.Q, ws.H, ws.evals, ws.evecs; passes = FP64 refinement passes of the eigensolver
-    void ritz(const float *S, int p, bool use32, int passes = 2, bool keep_hilo = false);
+    // with_xq: also leave X Q in ws.T1 and take H = S^T (X Q)
+    void ritz(const float *S, int p, bool use32, int passes = 2, bool with_xq = false);
     void normalize(float *z);                      // one column, in place
     double dot1(const float *a, const float *b);   // host read
 

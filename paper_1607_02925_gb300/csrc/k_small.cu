@@ -137,6 +137,107 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, 
     G[e] = (s0 + s1) + (s2 + s3);
 }
 
+// ---------------------------------------------------------------------------
+// Cross Gram H = (A^T B + B^T A)/2 for A, B dpad x p column-major (A optionally
+// the BF16 pair Ah + Al): with B = X (X^T A) this is the Rayleigh-Ritz matrix
+// A^T X X^T A from a d-long contraction.  64-row tiles, thread owns 4x4 blocks
+// over all (a, b) block pairs; FP32 sums over a tile added into FP64; partials
+// reduced (and symmetrised) in fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kCMaxBlk = 4;    // 784 block pairs at p = 112 -> up to 4 per thread
+
+__global__ void __launch_bounds__(256) cross_gram_kernel(const float *__restrict__ A,
+                                                         const __nv_bfloat16 *__restrict__ Ah,
+                                                         const __nv_bfloat16 *__restrict__ Al,
+                                                         const float *__restrict__ B, int64_t rows, int64_t ld,
+                                                         int p, int p4, double *__restrict__ part) {
+    extern __shared__ __align__(16) float cs_[];
+    float *As = cs_, *Bs = cs_ + kGR * p4;  // [kGR][p4] each
+    const int tid = threadIdx.x;
+    const int nb = p4 / 4;
+    const int npairs = nb * nb;
+    int ba[kCMaxBlk], bb[kCMaxBlk];
+    int nown = 0;
+#pragma unroll
+    for (int u = 0; u < kCMaxBlk; ++u) {
+        const int q = tid + 256 * u;
+        ba[u] = bb[u] = 0;
+        if (q < npairs) {
+            ba[u] = q / nb;
+            bb[u] = q % nb;
+            nown = u + 1;
+        }
+    }
+    double acc[kCMaxBlk][16];
+#pragma unroll
+    for (int u = 0; u < kCMaxBlk; ++u)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[u][e] = 0.0;
+    for (int64_t t0 = (int64_t)blockIdx.x * kGR; t0 < rows; t0 += (int64_t)gridDim.x * kGR) {
+        __syncthreads();
+        for (int e = tid; e < kGR * p4; e += 256) {
+            const int r = e % kGR, j = e / kGR;
+            const int64_t row = t0 + r;
+            float va = 0.0f, vb = 0.0f;
+            if (row < rows && j < p) {
+                const int64_t o = row + (int64_t)j * ld;
+                va = Ah ? __bfloat162float(Ah[o]) + __bfloat162float(Al[o]) : A[o];
+                vb = B[o];
+            }
+            As[r * p4 + j] = va;
+            Bs[r * p4 + j] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kCMaxBlk; ++u) {
+            if (u < nown) {
+                float f[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) f[e] = 0.0f;
+                const float *pa = As + 4 * ba[u];
+                const float *pb = Bs + 4 * bb[u];
+                for (int r = 0; r < kGR; ++r) {
+                    const float4 x = *reinterpret_cast<const float4 *>(pa + r * p4);
+                    const float4 y = *reinterpret_cast<const float4 *>(pb + r * p4);
+                    const float xa[4] = {x.x, x.y, x.z, x.w};
+                    const float ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) f[4 * i + j] = fmaf(xa[i], ya[j], f[4 * i + j]);
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[u][e] += (double)f[e];
+            }
+        }
+    }
+    double *out = part + (int64_t)blockIdx.x * p4 * p4;
+#pragma unroll
+    for (int u = 0; u < kCMaxBlk; ++u) {
+        if (u < nown) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) out[(4 * ba[u] + i) * p4 + 4 * bb[u] + j] = acc[u][4 * i + j];
+        }
+    }
+}
+
+// H[a + b p] = (sum_c part[c][a][b] + sum_c part[c][b][a]) / 2, chunks in order
+__global__ void cross_reduce_kernel(const double *__restrict__ part, int nparts, int p, int p4,
+                                    double *__restrict__ H) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p * p) return;
+    const int a = e % p, b = e / p;
+    const int64_t stride = (int64_t)p4 * p4;
+    double s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < nparts; ++c) {
+        s1 += part[c * stride + (int64_t)a * p4 + b];
+        s2 += part[c * stride + (int64_t)b * p4 + a];
+    }
+    H[e] = 0.5 * (s1 + s2);
+}
+
 // Rayleigh-Ritz on a basis S that is orthonormal only to rounding: with
 // G = S^T S = I + F and H = S^T A S, the Ritz values of the orthonormalised
 // basis S G^(-1/2) are those of G^(-1/2) H G^(-1/2) = H - (F H + H F)/2 + O(F^2)
@@ -659,6 +760,18 @@ void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_
     gram_kernel<true><<<nb, 256, smem, s>>>(A, Ah, Al, rows, 1, ld, p, p4, scratch);
     LRA_LAUNCHED();
     gram_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
+    LRA_LAUNCHED();
+}
+
+void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, const float *B,
+                int64_t rows, int64_t ld, int p, double *H, double *scratch) {
+    const int p4 = (int)round_up(p, 4);
+    const int nb = gram_blocks(rows);
+    const size_t smem = sizeof(float) * 2 * kGR * p4;
+    ensure_smem(cross_gram_kernel, (int)smem);
+    cross_gram_kernel<<<nb, 256, smem, s>>>(A, Ah, Al, B, rows, ld, p, p4, scratch);
+    LRA_LAUNCHED();
+    cross_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, H);
     LRA_LAUNCHED();
 }
 

@@ -87,6 +87,11 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
 // pair Ah + Al.  scratch >= gram_scratch(p) doubles
 void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, int64_t rows,
             int64_t ld, int p, double *G, double *scratch);
+// H = (A^T B + B^T A)/2 (FP64, p x p column-major) for A, B rows x p column-major
+// (leading dim ld; A read as the BF16 pair Ah + Al when Ah != nullptr).
+// scratch >= gram_scratch(p) doubles
+void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, const float *B,
+                int64_t rows, int64_t ld, int p, double *H, double *scratch);
 // Hc = 2H - (G H + H G)/2: Rayleigh-Ritz matrix of the orthonormalised basis
 // to first order in G - I (all p x p FP64 column-major, symmetric)
 void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc);
