@@ -94,6 +94,7 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
         b += sizeof(float) * (size_t)sp_items * PP;                 // partial
     else
         b += 2 * sizeof(__nv_bfloat16) * PP * (dpad + tc_ldy(n));  // Wb Yb
+    b += sizeof(double) * gram_scratch(pmax);  // side-stream Gram scratch
     return b;
 }
 
@@ -128,6 +129,10 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         evecs = alloc<double>(pp);
         eigwork = alloc<double>(sym_eig_work(pmax));
         gscr = alloc<double>(gram_scratch(pmax));
+        gscr2 = alloc<double>(gram_scratch(pmax));
+        LRA_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        LRA_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        LRA_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
         Gm = alloc<double>(pp);
         norms = alloc<double>(4);
         epi = alloc<double>(2 * (dpad / 16) + 8);
@@ -150,11 +155,15 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
     } catch (...) {
         for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
         allocs.clear();
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         throw;
     }
 }
 
 Workspace::~Workspace() {
+    if (side) cudaStreamSynchronize(side);
     if (astream) cudaStreamSynchronize(astream);
     for (auto &a : allocs) dev_free(ctx, a.first, a.second, astream);
     if (idx) dev_free(ctx, idx, sizeof(int32_t) * idx_cap, astream);
@@ -162,6 +171,9 @@ Workspace::~Workspace() {
     if (astream) cudaStreamSynchronize(astream);
     if (host) cudaFreeHost(host);
     if (hstat) cudaFreeHost(hstat);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
 }
 
 void Workspace::ensure_idx(int64_t m) {
@@ -435,6 +447,13 @@ lra_status Engine::qr_status() const {
 
 void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
     const int PP = pad_p(p);
+    // The FP64 Gram of the basis (for the orthogonality correction below)
+    // depends on S alone: it runs on the side stream, on the FP64 units, while
+    // the X passes stream X through the tensor cores.
+    LRA_CUDA(cudaEventRecord(ws_.ev_fork, s_));
+    LRA_CUDA(cudaStreamWaitEvent(ws_.side, ws_.ev_fork, 0));
+    gram64(ws_.side, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr2, tc(use32));
+    LRA_CUDA(cudaEventRecord(ws_.ev_join, ws_.side));
     xt_mul(S, p, ws_.Q, use32, with_xq);
     if (with_xq) {
         // X Q (kept in T1 for the warm start) and H = S^T (X Q): the Ritz
@@ -451,15 +470,15 @@ void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
         gram(s_, ws_.Q, mat_->n, PP, 1, p, ws_.H, ws_.gscr);
     }
     // S is orthonormal to FP32 rounding only; correct H to first order in
-    // S^T S - I, with the Gram of the basis the X pass actually used.
-    if (tc(use32))
-        gram64(s_, nullptr, ws_.Wb, ws_.Wb + (size_t)PP * mat_->dpad, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr);
-    else
-        gram64(s_, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr);
+    // S^T S - I, with the Gram of the basis the X pass actually used (its BF16
+    // pair on the tensor-core path).
+    LRA_CUDA(cudaStreamWaitEvent(s_, ws_.ev_join, 0));
     ortho_correct(s_, ws_.H, ws_.Gm, p, ws_.Hc);
     if (timer) timer->end();
     if (timer) timer->begin(KernelTimer::EIG, p);
-    sym_eig(s_, ws_.Hc, p, ws_.evals, ws_.evecs, ws_.eigwork, passes);
+    // inside the outer loop (with_xq) the basis is already close to the Ritz
+    // vectors and one refinement pass follows: looser sweeps suffice there
+    sym_eig(s_, ws_.Hc, p, ws_.evals, ws_.evecs, ws_.eigwork, passes, with_xq ? 1e-8 : 1e-10);
     if (timer) timer->end();
 }
 

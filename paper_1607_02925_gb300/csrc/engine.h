@@ -128,6 +128,9 @@ struct Workspace {
     float *Wr = nullptr, *Q = nullptr, *Y = nullptr, *Gp = nullptr;
     int nchunks = 0;  // capacity of Gp in dpad x PP chunks
     int nch = 1;      // chunks written by the last X Y pass
+    double *gscr2 = nullptr;  // Gram scratch of the side stream
+    cudaStream_t side = nullptr;          // second stream for work independent of the X passes
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *H = nullptr, *Hc = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;

@@ -1,5 +1,5 @@
 // p x p and d x p kernels of the outer loop: Gram matrices (FP64 accumulation),
-// Cholesky and triangular inverse (FP64, CholeskyQR2 of Algorithm 1's QR
+// Cholesky and triangular solve (FP64 / FP32, CholeskyQR2 of Algorithm 1's QR
 // step), right-multiplication of tall blocks by small matrices, the symmetric
 // eigenproblem of Algorithm 2 (cyclic Jacobi in one CTA, Rayleigh quotients in
 // FP64), and small vector helpers.
@@ -26,7 +26,7 @@ constexpr int kGMaxBlk = 2;    // 4x4 blocks per thread (406 blocks at p = 112 -
 
 template <bool kF64>
 __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, const __nv_bfloat16 *__restrict__ Ah,
-                                                   const __nv_bfloat16 *__restrict__ Al, int64_t rows,
+                                                   const __nv_bfloat16 *__restrict__ Al, int split, int64_t rows,
                                                    int64_t rs, int64_t cs, int p, int p4,
                                                    double *__restrict__ part) {
     using T = typename std::conditional<kF64, double, float>::type;
@@ -73,7 +73,15 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
             float v = 0.0f;
             if (row < rows && j < p) {
                 const int64_t o = row * rs + (int64_t)j * cs;
-                v = Ah ? __bfloat162float(Ah[o]) + __bfloat162float(Al[o]) : A[o];
+                if (Ah) {
+                    v = __bfloat162float(Ah[o]) + __bfloat162float(Al[o]);
+                } else {
+                    v = A[o];
+                    if (split) {  // the BF16 pair hi + lo of v, as the tensor-core passes see it
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                        v = __bfloat162float(hi) + __bfloat162float(__float2bfloat16_rn(v - __bfloat162float(hi)));
+                    }
+                }
             }
             As[r * p4 + j] = v;
         }
@@ -115,26 +123,27 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
 
 __global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, int p, int p4,
                                    double *__restrict__ G) {
+    // thread per entry (a, b) of the partials' row-major p4 x p4 layout (coalesced
+    // reads); only the stored blocks (a-block <= b-block) are summed, each into
+    // both G[a + b p] and G[b + a p]
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p * p) return;
-    int a = e % p, b = e / p;  // G column-major: G[a + b p]
-    if (a / 4 > b / 4) {
-        const int t = a;
-        a = b;
-        b = t;
-    }
+    if (e >= p4 * p4) return;
+    const int a = e / p4, b = e % p4;
+    if (a >= p || b >= p || a / 4 > b / 4) return;
     // four independent partial sums over interleaved parts, combined in a fixed order
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    const int64_t stride = (int64_t)p4 * p4, off = (int64_t)a * p4 + b;
+    const int64_t stride = (int64_t)p4 * p4;
     int c = 0;
     for (; c + 3 < nparts; c += 4) {
-        s0 += part[(c + 0) * stride + off];
-        s1 += part[(c + 1) * stride + off];
-        s2 += part[(c + 2) * stride + off];
-        s3 += part[(c + 3) * stride + off];
+        s0 += part[(c + 0) * stride + e];
+        s1 += part[(c + 1) * stride + e];
+        s2 += part[(c + 2) * stride + e];
+        s3 += part[(c + 3) * stride + e];
     }
-    for (; c < nparts; ++c) s0 += part[c * stride + off];
-    G[e] = (s0 + s1) + (s2 + s3);
+    for (; c < nparts; ++c) s0 += part[c * stride + e];
+    const double v = (s0 + s1) + (s2 + s3);
+    G[a + (int64_t)b * p] = v;
+    if (a / 4 < b / 4) G[b + (int64_t)a * p] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -223,19 +232,30 @@ __global__ void __launch_bounds__(256) cross_gram_kernel(const float *__restrict
     }
 }
 
-// H[a + b p] = (sum_c part[c][a][b] + sum_c part[c][b][a]) / 2, chunks in order
-__global__ void cross_reduce_kernel(const double *__restrict__ part, int nparts, int p, int p4,
-                                    double *__restrict__ H) {
+// C[a][b] = sum_c part[c][a][b] (chunks in order, coalesced), then
+// H[a + b p] = (C[a][b] + C[b][a]) / 2
+__global__ void cross_reduce_kernel(const double *__restrict__ part, int nparts, int p4,
+                                    double *__restrict__ C) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p4 * p4) return;
+    const int64_t stride = (int64_t)p4 * p4;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 0;
+    for (; c + 3 < nparts; c += 4) {
+        s0 += part[(c + 0) * stride + e];
+        s1 += part[(c + 1) * stride + e];
+        s2 += part[(c + 2) * stride + e];
+        s3 += part[(c + 3) * stride + e];
+    }
+    for (; c < nparts; ++c) s0 += part[c * stride + e];
+    C[e] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void symmetrise_kernel(const double *__restrict__ C, int p, int p4, double *__restrict__ H) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= p * p) return;
     const int a = e % p, b = e / p;
-    const int64_t stride = (int64_t)p4 * p4;
-    double s1 = 0.0, s2 = 0.0;
-    for (int c = 0; c < nparts; ++c) {
-        s1 += part[c * stride + (int64_t)a * p4 + b];
-        s2 += part[c * stride + (int64_t)b * p4 + a];
-    }
-    H[e] = 0.5 * (s1 + s2);
+    H[e] = 0.5 * (C[a * p4 + b] + C[b * p4 + a]);
 }
 
 // Rayleigh-Ritz on a basis S that is orthonormal only to rounding: with
@@ -264,62 +284,6 @@ __global__ void ortho_correct_kernel(const double *__restrict__ H, const double 
 int gram_blocks(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, kGR), 152)); }
 
 // ---------------------------------------------------------------------------
-// Cholesky G = L L^T (L = R^T) and L^-1, FP64, one CTA.  Rinv = (L^-1)^T as
-// FP32 row-major.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) chol_inv_kernel(const double *__restrict__ G, int p,
-                                                       float *__restrict__ Rinv, int *__restrict__ status) {
-    extern __shared__ __align__(16) double sm[];
-    const int ld = p + 1;
-    double *L = sm;            // [p][ld]
-    double *Li = sm + p * ld;  // [p][ld]
-    __shared__ int bad;
-    const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    for (int e = tid; e < p * p; e += 256) {
-        const int a = e % p, b = e / p;
-        L[a * ld + b] = G[e];
-        Li[a * ld + b] = 0.0;
-    }
-    __syncthreads();
-    for (int c = 0; c < p; ++c) {
-        if (tid == 0) {
-            const double piv = L[c * ld + c];
-            if (!(piv > 0.0) || !isfinite(piv)) {
-                bad = 1;
-                L[c * ld + c] = 1.0;
-            } else {
-                L[c * ld + c] = sqrt(piv);
-            }
-        }
-        __syncthreads();
-        const double dcc = L[c * ld + c];
-        for (int r = c + 1 + tid; r < p; r += 256) L[r * ld + c] /= dcc;
-        __syncthreads();
-        const int m = p - c - 1;
-        for (int e = tid; e < m * m; e += 256) {
-            const int r = c + 1 + e / m, s = c + 1 + e % m;
-            if (s <= r) L[r * ld + s] -= L[r * ld + c] * L[s * ld + c];
-        }
-        __syncthreads();
-    }
-    // column j of L^-1 by forward substitution (one thread per column)
-    for (int j = tid; j < p; j += 256) {
-        for (int i = j; i < p; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int k = j; k < i; ++k) s -= L[i * ld + k] * Li[k * ld + j];
-            Li[i * ld + j] = s / L[i * ld + i];
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < p * p; e += 256) {
-        const int a = e / p, b = e % p;  // Rinv[a][b] = Li[b][a] (upper triangular)
-        Rinv[e] = (float)Li[b * ld + a];
-    }
-    if (tid == 0) *status = bad;
-}
-
-// ---------------------------------------------------------------------------
 // Cholesky G = L L^T in FP64, one CTA, one barrier per column: step c reads
 // column c (not yet scaled) and updates the trailing lower triangle; the
 // scaling of column c by its pivot is applied when R is written out.
@@ -346,13 +310,12 @@ __global__ void __launch_bounds__(256) chol_kernel(const double *__restrict__ G,
         }
         if (tid == 0) piv[c] = sqrt(dd);
         const double inv = 1.0 / dd;  // (l_rc / sqrt dd)(l_sc / sqrt dd) = l_rc l_sc / dd
-        const int m = p - c - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int r = e / m, s = e % m;
-            if (s <= r) {
-                const int rr = c + 1 + r, ss = c + 1 + s;
-                L[rr * ld + ss] -= L[rr * ld + c] * L[ss * ld + c] * inv;
-            }
+        // trailing update of the lower triangle: warp per row, lanes along the
+        // row; column c is only read in this step
+        const int lane = tid & 31, nw = nt >> 5;
+        for (int rr = c + 1 + (tid >> 5); rr < p; rr += nw) {
+            const double lr = L[rr * ld + c] * inv;
+            for (int ss = c + 1 + lane; ss <= rr; ss += 32) L[rr * ld + ss] -= lr * L[ss * ld + c];
         }
         __syncthreads();
     }
@@ -370,22 +333,32 @@ __global__ void __launch_bounds__(256) chol_kernel(const double *__restrict__ G,
 
 // Q = W R^-1 row by row (forward substitution q_j = (w_j - sum_{l<j} q_l R_lj) / R_jj),
 // one thread per row; R in shared memory, the row's q in shared memory.
-__global__ void __launch_bounds__(128) trsm_rows_kernel(const float *__restrict__ W, int64_t rows,
-                                                        int64_t ld, int p, const float *__restrict__ R,
-                                                        float *__restrict__ Q) {
+constexpr int kTrsmRows = 64;  // rows (threads) per CTA
+
+__global__ void __launch_bounds__(kTrsmRows) trsm_rows_kernel(const float *__restrict__ W, int64_t rows,
+                                                              int64_t ld, int p, const float *__restrict__ R,
+                                                              float *__restrict__ Q) {
     extern __shared__ __align__(16) float sr[];
     float *Rs = sr;               // [p][p]
-    float *qs = sr + p * p;       // [p][128]
+    float *qs = sr + p * p;       // [p][kTrsmRows]
     const int tid = threadIdx.x;
-    for (int e = tid; e < p * p; e += 128) Rs[e] = R[e];
+    for (int e = tid; e < p * p; e += kTrsmRows) Rs[e] = R[e];
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * 128 + tid;
+    const int64_t r = (int64_t)blockIdx.x * kTrsmRows + tid;
     if (r >= rows) return;
     for (int j = 0; j < p; ++j) {
-        float s = W[r + (int64_t)j * ld];
-        for (int l = 0; l < j; ++l) s = fmaf(-qs[l * 128 + tid], Rs[l * p + j], s);
-        const float q = s / Rs[j * p + j];
-        qs[j * 128 + tid] = q;
+        // four interleaved partial sums shorten the dependent chain
+        float s0 = W[r + (int64_t)j * ld], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int l = 0;
+        for (; l + 3 < j; l += 4) {
+            s0 = fmaf(-qs[(l + 0) * kTrsmRows + tid], Rs[(l + 0) * p + j], s0);
+            s1 = fmaf(-qs[(l + 1) * kTrsmRows + tid], Rs[(l + 1) * p + j], s1);
+            s2 = fmaf(-qs[(l + 2) * kTrsmRows + tid], Rs[(l + 2) * p + j], s2);
+            s3 = fmaf(-qs[(l + 3) * kTrsmRows + tid], Rs[(l + 3) * p + j], s3);
+        }
+        for (; l < j; ++l) s0 = fmaf(-qs[l * kTrsmRows + tid], Rs[l * p + j], s0);
+        const float q = ((s0 + s1) + (s2 + s3)) / Rs[j * p + j];
+        qs[j * kTrsmRows + tid] = q;
         Q[r + (int64_t)j * ld] = q;
     }
 }
@@ -453,7 +426,7 @@ __device__ __forceinline__ int rr_partner(int a, int r, int m) {
 }
 
 __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ H, int p,
-                                                     double *__restrict__ Vout, int max_sweeps) {
+                                                     double *__restrict__ Vout, int max_sweeps, double tol) {
     extern __shared__ __align__(16) float jb[];
     const int p2 = p + (p & 1);
     const int ld = p2 + 1;
@@ -498,9 +471,9 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double *__restrict__ 
                 o += red_off[w];
                 t += red_tot[w];
             }
-            // squared relative off-diagonal mass 1e-10: the FP64 refinement that
-            // follows squares the remaining rotation angles
-            stop = (o <= 1e-10 * t || (sweep > 0 && !rotated)) ? 1 : 0;
+            // squared relative off-diagonal mass below tol: the FP64 refinement
+            // that follows squares the remaining rotation angles
+            stop = (o <= tol * t || (sweep > 0 && !rotated)) ? 1 : 0;
             rotated = 0;
         }
         __syncthreads();
@@ -745,21 +718,21 @@ void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, 
     const int nb = gram_blocks(rows);
     const size_t smem = sizeof(float) * kGR * p4;
     LRA_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double) * nb * p4 * p4, s));
-    gram_kernel<false><<<nb, 256, smem, s>>>(A, nullptr, nullptr, rows, rs, cs, p, p4, scratch);
+    gram_kernel<false><<<nb, 256, smem, s>>>(A, nullptr, nullptr, 0, rows, rs, cs, p, p4, scratch);
     LRA_LAUNCHED();
-    gram_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
+    gram_reduce_kernel<<<(unsigned)ceil_div(p4 * p4, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
     LRA_LAUNCHED();
 }
 
 void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, int64_t rows,
-            int64_t ld, int p, double *G, double *scratch) {
+            int64_t ld, int p, double *G, double *scratch, bool split) {
     const int p4 = (int)round_up(p, 4);
     const int nb = gram_blocks(rows);
     const size_t smem = sizeof(float) * kGR * p4;
     LRA_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double) * nb * p4 * p4, s));
-    gram_kernel<true><<<nb, 256, smem, s>>>(A, Ah, Al, rows, 1, ld, p, p4, scratch);
+    gram_kernel<true><<<nb, 256, smem, s>>>(A, Ah, Al, split ? 1 : 0, rows, 1, ld, p, p4, scratch);
     LRA_LAUNCHED();
-    gram_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
+    gram_reduce_kernel<<<(unsigned)ceil_div(p4 * p4, 256), 256, 0, s>>>(scratch, nb, p, p4, G);
     LRA_LAUNCHED();
 }
 
@@ -771,7 +744,10 @@ void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const _
     ensure_smem(cross_gram_kernel, (int)smem);
     cross_gram_kernel<<<nb, 256, smem, s>>>(A, Ah, Al, B, rows, ld, p, p4, scratch);
     LRA_LAUNCHED();
-    cross_reduce_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(scratch, nb, p, p4, H);
+    double *C = scratch + (int64_t)nb * p4 * p4;  // gram_scratch holds 2 x 152 partials
+    cross_reduce_kernel<<<(unsigned)ceil_div(p4 * p4, 256), 256, 0, s>>>(scratch, nb, p4, C);
+    LRA_LAUNCHED();
+    symmetrise_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(C, p, p4, H);
     LRA_LAUNCHED();
 }
 
@@ -789,18 +765,12 @@ void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
 }
 
 void trsm_rows(cudaStream_t s, const float *W, int64_t rows, int64_t ld, int p, const float *R, float *Q) {
-    const size_t smem = sizeof(float) * ((size_t)p * p + (size_t)p * 128);
+    const size_t smem = sizeof(float) * ((size_t)p * p + (size_t)p * kTrsmRows);
     ensure_smem(trsm_rows_kernel, (int)smem);
-    trsm_rows_kernel<<<(unsigned)ceil_div(rows, 128), 128, smem, s>>>(W, rows, ld, p, R, Q);
+    trsm_rows_kernel<<<(unsigned)ceil_div(rows, kTrsmRows), kTrsmRows, smem, s>>>(W, rows, ld, p, R, Q);
     LRA_LAUNCHED();
 }
 
-void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status) {
-    const size_t smem = sizeof(double) * 2 * p * (p + 1);
-    ensure_smem(chol_inv_kernel, (int)smem);
-    chol_inv_kernel<<<1, 256, smem, s>>>(G, p, Rinv, status);
-    LRA_LAUNCHED();
-}
 
 void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int64_t acs, int p,
                  const float *T, int q, float *Out, int64_t ors, int64_t ocs) {
@@ -815,7 +785,8 @@ void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int6
 // Newton-Schulz orthonormalisation V <- V (3 I - V^T V) / 2, B = V^T H V, the
 // first-order rotation V <- V (I + E) that annihilates B's off-diagonal to
 // second order, a second orthonormalisation, and FP64 Rayleigh quotients.
-void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes) {
+void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes,
+             double jacobi_tol) {
     const int p2 = p + (p & 1);
     const size_t pp = (size_t)p * p;
     double *V = work;           // p*p
@@ -826,7 +797,7 @@ void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evec
     const size_t smem = sizeof(float) * (4 * p2 * (p2 + 1) + 3 * p2);
     ensure_smem(jacobi_kernel, (int)smem);
     const int nt = p2 <= 16 ? 128 : 512;
-    jacobi_kernel<<<1, nt, smem, s>>>(H, p, V, 40);
+    jacobi_kernel<<<1, nt, smem, s>>>(H, p, V, 40, jacobi_tol);
     LRA_LAUNCHED();
     auto gemm = [&](const double *A, const double *B, int ta, double alpha, double beta, double *C) {
         gemm_pp_kernel<<<p, 128, 0, s>>>(A, B, p, ta, alpha, beta, C);

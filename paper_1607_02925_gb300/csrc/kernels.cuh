@@ -83,10 +83,11 @@ int64_t gram_scratch(int p);
 void gram(cudaStream_t s, const float *A, int64_t rows, int64_t rs, int64_t cs, int p, double *G,
           double *scratch);
 // G = A^T A with every product accumulated in FP64; A column-major rows x p
-// (leading dimension ld), read as FP32 A or, when Ah != nullptr, as the BF16
-// pair Ah + Al.  scratch >= gram_scratch(p) doubles
+// (leading dimension ld), read as FP32 A, as the BF16 pair Ah + Al when
+// Ah != nullptr, or as the BF16 pair of A (round-to-nearest hi, then lo of the
+// remainder) when split.  scratch >= gram_scratch(p) doubles
 void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, int64_t rows,
-            int64_t ld, int p, double *G, double *scratch);
+            int64_t ld, int p, double *G, double *scratch, bool split = false);
 // H = (A^T B + B^T A)/2 (FP64, p x p column-major) for A, B rows x p column-major
 // (leading dim ld; A read as the BF16 pair Ah + Al when Ah != nullptr).
 // scratch >= gram_scratch(p) doubles
@@ -95,9 +96,6 @@ void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const _
 // Hc = 2H - (G H + H G)/2: Rayleigh-Ritz matrix of the orthonormalised basis
 // to first order in G - I (all p x p FP64 column-major, symmetric)
 void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc);
-// Cholesky G = R^T R (upper R), Rinv = R^-1 as FP32 p x p row-major;
-// status[0] = 0 ok / 1 not positive definite
-void chol_inv(cudaStream_t s, const double *G, int p, float *Rinv, int *status);
 // Cholesky G = R^T R in FP64 (one barrier per column); R upper FP32 row-major
 void chol(cudaStream_t s, const double *G, int p, float *R, int *status);
 // Q = W R^-1 by row-wise forward substitution (W, Q rows x p column-major)
@@ -109,7 +107,10 @@ void apply_right(cudaStream_t s, const float *A, int64_t rows, int64_t ars, int6
 // evecs column-major FP64 (largest |entry| positive).  work >= sym_eig_work(p) doubles.
 int64_t sym_eig_work(int p);
 // passes: FP64 refinement passes after the FP32 sweeps (each squares the residual rotation)
-void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes = 2);
+// jacobi_tol: the FP32 sweeps stop once the squared off-diagonal mass is below
+// jacobi_tol times the total (1e-10 by default; the refinement squares what is left)
+void sym_eig(cudaStream_t s, const double *H, int p, double *evals, double *evecs, double *work, int passes = 2,
+             double jacobi_tol = 1e-10);
 // P (p x p FP32 row-major) = V_k diag(f(rho)) V_k^T with f = 1/(lam - rho):
 // the Galerkin inverse (lam I - H)^-1 on the Ritz basis.  kcols = p.
 void ritz_inverse(cudaStream_t s, const double *evecs, const double *evals, int p, double lam,
