@@ -73,6 +73,21 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
+def recorded_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.txt
+    (an ncu capture of the current kernel), or None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and not line.startswith("#") and parts[0] == workload and parts[1] == kernel:
+                    return int(parts[2])
+    except OSError:
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -460,6 +475,7 @@ def run_lra(args):
                     "unit": "GB/s", "frac": bytes_l / t_l / hbm, "traffic": None}
         names = {("xtw", True): "xtw_tc_kernel", ("xy", True): "xy_tc_kernel",
                  ("xtw", False): "spmm_xt_kernel", ("xy", False): "spmm_x_kernel"}
+        roof["traffic"] = recorded_traffic(args.workload, names[(dom, src.tensor)])
         roof.update({"kernel": names[(dom, src.tensor)],
                      "launches": cnt[dom], "ms_per_launch": t_l * 1e3,
                      "algorithmic_bytes_per_launch": bytes_l,

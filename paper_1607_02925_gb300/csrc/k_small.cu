@@ -293,18 +293,20 @@ __global__ void __launch_bounds__(256) chol_kernel(const double *__restrict__ G,
                                                    float *__restrict__ R, int *__restrict__ status) {
     extern __shared__ __align__(16) double sl[];
     const int ld = p + 1;
-    double *L = sl;           // [p][ld]
-    double *piv = sl + p * ld;  // [p]
+    double *L = sl;               // [p][ld]
+    double *piv = sl + p * ld;    // [p]
+    double *g0 = piv + p;         // [p] original diagonal
     __shared__ int bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) bad = 0;
     for (int e = tid; e < p * p; e += nt) L[(e % p) * ld + e / p] = G[e];
+    for (int c = tid; c < p; c += nt) g0[c] = G[c + (int64_t)c * p];
     __syncthreads();
     for (int c = 0; c < p; ++c) {
         double dd = L[c * ld + c];
         // a pivot at the rounding level of its original diagonal means the
         // columns are linearly dependent to working precision
-        if (!(dd > 1e-14 * G[c + (int64_t)c * p]) || !isfinite(dd)) {
+        if (!(dd > 1e-14 * g0[c]) || !isfinite(dd)) {
             if (tid == 0) bad = 1;
             dd = 1.0;
         }
@@ -757,7 +759,7 @@ void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, doub
 }
 
 void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
-    const size_t smem = sizeof(double) * ((size_t)p * (p + 1) + p);
+    const size_t smem = sizeof(double) * ((size_t)p * (p + 1) + 2 * p);
     ensure_smem(chol_kernel, (int)smem);
     const int nt = p <= 48 ? 128 : 256;
     chol_kernel<<<1, nt, smem, s>>>(G, p, R, status);
