@@ -255,10 +255,10 @@ def _clib():
     vp = ctypes.c_void_p
     for name in ("oracle_svrg_inner_f64", "oracle_svrg_inner_f32"):
         fn = getattr(lib, name)
-        fn.argtypes = [i64, i64, vp, i64, vp, i64, vp, dbl, dbl, vp, vp, vp]
+        fn.argtypes = [i64, i64, vp, i64, vp, i64, i64, vp, dbl, dbl, vp, vp, vp]
         fn.restype = None
     fn = lib.oracle_svrg_inner_csc
-    fn.argtypes = [i64, i64, vp, vp, vp, vp, i64, vp, dbl, dbl, vp, vp, vp]
+    fn.argtypes = [i64, i64, vp, vp, vp, vp, i64, i64, vp, dbl, dbl, vp, vp, vp]
     fn.restype = None
     _CLIB = lib
     return lib
@@ -276,11 +276,16 @@ def build_c() -> str:
 
 
 def svrg_epoch(Xt: np.ndarray, W: np.ndarray, Wt: np.ndarray, M: np.ndarray,
-               idx: np.ndarray, c: np.ndarray, eta: float, lam: float) -> np.ndarray:
-    """m variance-reduced steps from W (one per sampled index); returns new W.
+               idx: np.ndarray, c: np.ndarray, eta: float, lam: float, batch: int = 1) -> np.ndarray:
+    """len(idx) / batch variance-reduced steps from W; returns the new W.
 
-    Step: r = x_i^T (W - Wt); W <- W - eta [lambda (W - Wt) - c_i x_i r + M].
+    Step (batch b, samples i_1..i_b): r_u = x_{i_u}^T (W - Wt) for every u at the
+    same W; W <- W - eta [lambda (W - Wt) - (1/b) sum_u c_{i_u} x_{i_u} r_u + M].
+    b = 1 is the step of Sec. 2.3's SVRGsolve.
     """
+    if len(idx) % batch:
+        raise ValueError("index sequence is not a whole number of batches")
+    m = len(idx) // batch
     lib = _clib()
     d, p = W.shape
     Wc = np.array(W, dtype=np.float64, order="F", copy=True)
@@ -295,7 +300,7 @@ def svrg_epoch(Xt: np.ndarray, W: np.ndarray, Wt: np.ndarray, M: np.ndarray,
         rowidx = np.ascontiguousarray(Xr.indices, dtype=np.int32)
         val = np.ascontiguousarray(Xr.data, dtype=np.float32)
         lib.oracle_svrg_inner_csc(d, p, colptr.ctypes.data, rowidx.ctypes.data, val.ctypes.data,
-                                  idx64.ctypes.data, idx64.shape[0], c64.ctypes.data, float(eta),
+                                  idx64.ctypes.data, m, batch, c64.ctypes.data, float(eta),
                                   float(lam), Wtc.ctypes.data, Mc.ctypes.data, Wc.ctypes.data)
         return np.array(Wc)
     Xc = np.ascontiguousarray(Xt)
@@ -306,7 +311,7 @@ def svrg_epoch(Xt: np.ndarray, W: np.ndarray, Wt: np.ndarray, M: np.ndarray,
     else:
         Xc = Xc.astype(np.float64)
         fn = lib.oracle_svrg_inner_f64
-    fn(d, p, Xc.ctypes.data, Xc.shape[1], idx64.ctypes.data, idx64.shape[0],
+    fn(d, p, Xc.ctypes.data, Xc.shape[1], idx64.ctypes.data, m, batch,
        c64.ctypes.data, float(eta), float(lam), Wtc.ctypes.data, Mc.ctypes.data,
        Wc.ctypes.data)
     return np.array(Wc)
@@ -328,6 +333,7 @@ class Options:
     sampling: int = SAMPLE_IMPORTANCE
     warm_start: int = 1
     max_shift_rounds: int = 30
+    batch: int = 1              # samples per inner step (minibatch reading; 1 = Sec. 2.3)
 
 
 @dataclass
@@ -355,12 +361,16 @@ class Context:
         self.x_passes = 0
 
     def step_params(self, lam: float, mu: float, lam1_up: float) -> tuple[float, int]:
-        """eta = theta_eta mu/(lambda^2 + kappa lambda1_up), m = ceil(theta_m/(eta mu))."""
+        """eta = theta_eta mu/(lambda^2 + kappa lambda1_up / b), m = ceil(theta_m/(eta mu))
+        steps of b samples (b = 1: the step size and epoch length of Theorem 3's
+        SVRG; a batch of b averages the stochastic term, dividing its variance,
+        the kappa lambda1_up term, by b).  At most m_max samples per epoch."""
         o = self.opts
-        eta = o.theta_eta * mu / (lam * lam + self.table.kappa * lam1_up)
+        b = max(1, int(o.batch))
+        eta = o.theta_eta * mu / (lam * lam + self.table.kappa * lam1_up / b)
         m = int(math.ceil(o.theta_m / (eta * mu)))
         m_max = o.m_max if o.m_max > 0 else 50 * self.n
-        return eta, min(m, m_max)
+        return eta, min(m, max(1, m_max // b))
 
     def svrg_solve(self, B: np.ndarray, W0: np.ndarray, lam: float, mu: float,
                    lam1_up: float, Y0: np.ndarray | None = None):
@@ -405,8 +415,9 @@ class Context:
             best = min(best, res)
             prev = res
             key = stream_key(self.seed, STREAM_SVRG, solve_id, e)
-            idx = sample_indices(self.table, key, m)
-            W = svrg_epoch(self.Xt, Wt, Wt, M, idx, self.table.c, eta, lam)
+            b = max(1, int(o.batch))
+            idx = sample_indices(self.table, key, m * b)
+            W = svrg_epoch(self.Xt, Wt, Wt, M, idx, self.table.c, eta, lam, b)
             st.inner_steps += m
             self.inner_steps += m
         return W, st
