@@ -26,7 +26,7 @@ using namespace tc;
 constexpr int kBM = 128;                // rows of the MMA tile
 constexpr int kBK = 64;                 // K elements per pipeline stage (128 B of BF16)
 constexpr int kATile = kBM * kBK * 2;   // 16 KB
-constexpr int kAccCols = 128;           // TMEM columns per accumulator (PP <= 112)
+constexpr int kAccCols1 = 128;          // TMEM columns per accumulator (PP <= 112)
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -34,58 +34,84 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 
 // NA = 1: X stored in BF16.  NA = 2: X stored in FP32 and streamed as its
 // BF16 hi + lo pair (x = hi + lo + r, |r| <= 2^-17 |x|).
-// MT = number of 128-row M tiles per CTA sharing each small-operand tile (two
-// accumulators in TMEM): halves the small operand's L2 traffic and doubles the
-// X bytes in flight per stage.
+// MT = number of 128-row M tiles per work tile sharing each small-operand tile
+// (MT accumulators): halves the small operand's L2 traffic and doubles the X
+// bytes in flight per stage.
+//
+// The kernels are persistent: one CTA per SM walks the work tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 (one lane) streams the
+// stages by TMA through a ring that runs on across tiles, warp 1 (one lane)
+// issues the MMAs, and warps 2-5 drain the accumulators.  TMEM holds two
+// accumulator sets, so the drain of tile t overlaps the MMAs of tile t + 1.
 template <int PP, int NA, int MT>
 struct Tile {
     static constexpr int kA1 = NA * kATile;         // one M tile: hi [+ lo]
     static constexpr int kA = MT * kA1;
     static constexpr int kB = PP * 128;             // one of hi / lo: PP rows x 128 B
     static constexpr int kStage = kA + 2 * kB;      // multiple of 1024
-    static constexpr int kFit = (220 * 1024) / kStage;
-    static constexpr int kStages = MT == 1 ? (NA == 1 ? (PP <= 64 ? 3 : 4) : (kStage <= 50 * 1024 ? 4 : 3))
-                                           : (kFit > 4 ? 4 : kFit);
-    static constexpr int kSmem = kStages * kStage + 1024 + 256;
-    static constexpr uint32_t kTmemCols = MT == 1 ? 128u : 256u;
+    static constexpr int kFit = (216 * 1024) / kStage;
+    static constexpr int kStages = kFit > 6 ? 6 : kFit;
+    static constexpr int kSmem = kStages * kStage + 1024 + 512;
+    static constexpr uint32_t kAccCols = MT * kAccCols1;  // one accumulator set
+    static constexpr uint32_t kTmemCols = 2 * kAccCols;   // two sets (<= 512)
     static_assert(kStages >= 2, "pipeline needs two stages");
 };
 
-// Shared tail of both kernels: barriers and the TMEM address slot after the stages.
+constexpr int kThreads = 192;  // producer warp, MMA warp, four epilogue warps
+
+// Control block after the stages: ring barriers, accumulator barriers, TMEM address.
 struct Ctl {
-    uint64_t full[4], empty[4], accum;
+    uint64_t full[6], empty[6], accf[2], acce[2];
     uint32_t tmem;
 };
 
+template <int PP, int NA, int MT>
+__device__ __forceinline__ void init_ctl(Ctl *ctl) {
+    using T = Tile<PP, NA, MT>;
+    for (int s = 0; s < T::kStages; ++s) {
+        mbar_init(&ctl->full[s], 1);
+        mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+        mbar_init(&ctl->accf[b], 1);
+        mbar_init(&ctl->acce[b], 4);  // one arrival per epilogue warp
+    }
+    fence_barrier_init();
+}
+
+// After an error the producer waits (bounded) for the stages it still has in
+// flight, so that no TMA write lands after the CTA has exited.
+template <int S>
+__device__ __forceinline__ void drain_issued(Ctl *ctl, int issued) {
+    for (int g = (issued > S ? issued - S : 0); g < issued; ++g)
+        mbar_wait(&ctl->full[g % S], (uint32_t)(g / S) & 1u);
+}
+
 // ---------------------------------------------------------------------------
-// Y = X^T W
+// Y = X^T W: work tile = MT x 128 data points (rows of X^T), K = d
 // ---------------------------------------------------------------------------
 template <int PP, int NA, int MT>
-__global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                        const __grid_constant__ CUtensorMap tmXl,
-                                                        const __grid_constant__ CUtensorMap tmW,
-                                                        int nkb, int64_t n, float *__restrict__ Y32,
-                                                        __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
-                                                        int *__restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                             const __grid_constant__ CUtensorMap tmXl,
+                                                             const __grid_constant__ CUtensorMap tmW,
+                                                             int nkb, int64_t n, float *__restrict__ Y32,
+                                                             __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
+                                                             int *__restrict__ err) {
     using T = Tile<PP, NA, MT>;
+    constexpr int S = T::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + S * T::kStage);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i0 = (int64_t)blockIdx.x * kBM * MT;
+    const int ntiles = (int)((n + kBM * MT - 1) / (kBM * MT));
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < T::kStages; ++s) {
-            mbar_init(&ctl->full[s], 1);
-            mbar_init(&ctl->empty[s], 1);
-        }
-        mbar_init(&ctl->accum, 1);
-        fence_barrier_init();
+        init_ctl<PP, NA, MT>(ctl);
         prefetch_tmap(&tmX);
         if (NA == 2) prefetch_tmap(&tmXl);
         prefetch_tmap(&tmW);
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(&ctl->tmem, T::kTmemCols);
         tmem_relinquish();
     }
@@ -95,127 +121,158 @@ __global__ void __launch_bounds__(128, 1) xtw_tc_kernel(const __grid_constant__ 
     const uint32_t tmem = ctl->tmem;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % T::kStages;
-            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
-            if (!mbar_wait(&ctl->empty[st], ph ^ 1u)) {
-                atomicOr(err, kErrTimeout);
-                break;
-            }
-            uint8_t *a = smem + st * T::kStage;
-            mbar_expect_tx(&ctl->full[st], T::kStage);
+        // TMA producer: one ring position per (tile, k-block)
+        int g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t i0 = (int64_t)tile * kBM * MT;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int st = g % S;
+                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u)) {
+                    atomicOr(err, kErrTimeout);
+                    ok = false;
+                    break;
+                }
+                uint8_t *a = smem + st * T::kStage;
+                mbar_expect_tx(&ctl->full[st], T::kStage);
 #pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const int row = (int)i0 + mt * kBM;
-                tma_load_2d(a + mt * T::kA1, &tmX, kb * kBK, row, &ctl->full[st]);
-                if (NA == 2) tma_load_2d(a + mt * T::kA1 + kATile, &tmXl, kb * kBK, row, &ctl->full[st]);
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int row = (int)i0 + mt * kBM;
+                    tma_load_2d(a + mt * T::kA1, &tmX, kb * kBK, row, &ctl->full[st]);
+                    if (NA == 2) tma_load_2d(a + mt * T::kA1 + kATile, &tmXl, kb * kBK, row, &ctl->full[st]);
+                }
+                tma_load_2d(a + T::kA, &tmW, kb * kBK, 0, &ctl->full[st]);
+                tma_load_2d(a + T::kA + T::kB, &tmW, kb * kBK, PP, &ctl->full[st]);
             }
-            tma_load_2d(a + T::kA, &tmW, kb * kBK, 0, &ctl->full[st]);
-            tma_load_2d(a + T::kA + T::kB, &tmW, kb * kBK, PP, &ctl->full[st]);
         }
+        if (!ok) drain_issued<S>(ctl, g);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer: tile lt accumulates into set lt & 1
         constexpr uint32_t idesc = instr_desc(1, 0, 0, PP, kBM);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % T::kStages;
-            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
-            if (!mbar_wait(&ctl->full[st], ph)) {
+        int g = 0, lt = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (lt >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((lt >> 1) - 1) & 1u)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
             tc_fence_after();
-            const uint32_t a = smem_u32(smem + st * T::kStage);
-            const uint32_t bh = a + T::kA, bl = bh + T::kB;
-#pragma unroll
-            for (int ks = 0; ks < kBK / 16; ++ks) {
-                const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const uint32_t am = a + mt * T::kA1;
-                    const uint32_t acc = tmem + mt * kAccCols;
-                    const uint64_t ad = sw128_desc(am + ks * 32, 16, 1024);
-                    mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
-                    mma_f16(acc, ad, bld, idesc, 1u);
-                    if (NA == 2) mma_f16(acc, sw128_desc(am + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+            const uint32_t accb = tmem + buf * T::kAccCols;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int st = g % S;
+                if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u)) {
+                    atomicOr(err, kErrTimeout);
+                    ok = false;
+                    break;
                 }
+                tc_fence_after();
+                const uint32_t a = smem_u32(smem + st * T::kStage);
+                const uint32_t bh = a + T::kA, bl = bh + T::kB;
+#pragma unroll
+                for (int ks = 0; ks < kBK / 16; ++ks) {
+                    const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                    const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const uint32_t am = a + mt * T::kA1;
+                        const uint32_t acc = accb + mt * kAccCols1;
+                        const uint64_t ad = sw128_desc(am + ks * 32, 16, 1024);
+                        mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
+                        mma_f16(acc, ad, bld, idesc, 1u);
+                        if (NA == 2) mma_f16(acc, sw128_desc(am + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+                    }
+                }
+                mma_commit(&ctl->empty[st]);
             }
-            mma_commit(&ctl->empty[st]);
+            if (ok) mma_commit(&ctl->accf[buf]);
         }
-        mma_commit(&ctl->accum);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows i0 + 128 mt + 32w + lane)
-    const bool ok = mbar_wait(&ctl->accum, 0);
-    tc_fence_after();
-    if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-    } else {
+    } else if (warp >= 2) {
+        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 of both M tiles
+        const int q = warp & 3;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (!mbar_wait(&ctl->accf[buf], (uint32_t)(lt >> 1) & 1u)) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const int64_t i0 = (int64_t)tile * kBM * MT;
 #pragma unroll 1
-      for (int mt = 0; mt < MT; ++mt) {
-        const int64_t i = i0 + mt * kBM + warp * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + mt * kAccCols;
+            for (int mt = 0; mt < MT; ++mt) {
+                const int64_t i = i0 + mt * kBM + q * 32 + lane;
+                const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
 #pragma unroll
-        for (int c = 0; c < PP; c += 16) {
-            float v[16];
-            tmem_ld16(tl + c, v);
-            if (i < n) {
-                if (Y32) {
-                    float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
+                for (int c = 0; c < PP; c += 16) {
+                    float v[16];
+                    tmem_ld16(tl + c, v);
+                    if (i < n) {
+                        if (Y32) {
+                            float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
-                if (Yb) {
+                            for (int u = 0; u < 4; ++u)
+                                dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                        }
+                        if (Yb) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
-                        const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
-                        Yb[(int64_t)(c + j) * ldy + i] = hi;
-                        Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
+                            for (int j = 0; j < 16; ++j) {
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                                const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                                Yb[(int64_t)(c + j) * ldy + i] = hi;
+                                Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
+                            }
+                        }
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->acce[buf]);
         }
-      }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, T::kTmemCols);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, T::kTmemCols);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Partial G = X[rows, chunk] Y[chunk, :]  (X is the MN-major operand here)
+// Partial G = X[rows, chunk] Y[chunk, :] (X is the MN-major operand here).
+// Work tile = (MT x 128 rows of X, one column chunk); row tiles vary fastest,
+// so the CTAs in flight share the chunk's Y tiles in L2.
 // ---------------------------------------------------------------------------
 template <int PP, int NA, int MT>
-__global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                       const __grid_constant__ CUtensorMap tmXl,
-                                                       const __grid_constant__ CUtensorMap tmY,
-                                                       int64_t cols_per_chunk, int64_t n, int64_t dpad,
-                                                       float *__restrict__ Gp, int *__restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                            const __grid_constant__ CUtensorMap tmXl,
+                                                            const __grid_constant__ CUtensorMap tmY,
+                                                            int64_t cols_per_chunk, int nchunks, int64_t n,
+                                                            int64_t dpad, float *__restrict__ Gp,
+                                                            int *__restrict__ err) {
     using T = Tile<PP, NA, MT>;
+    constexpr int S = T::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem + T::kStages * T::kStage);
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + S * T::kStage);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * kBM * MT;
-    const int64_t c0 = (int64_t)blockIdx.y * cols_per_chunk;
-    const int64_t c1 = (c0 + cols_per_chunk < n) ? c0 + cols_per_chunk : n;
-    const int nkb = c1 > c0 ? (int)((c1 - c0 + kBK - 1) / kBK) : 0;
+    const int rtiles = (int)((dpad + kBM * MT - 1) / (kBM * MT));
+    const int ntiles = rtiles * nchunks;
+    // K blocks of a chunk (0 for an empty chunk)
+    auto chunk_kb = [&](int ch, int64_t &c0) {
+        c0 = (int64_t)ch * cols_per_chunk;
+        const int64_t c1 = (c0 + cols_per_chunk < n) ? c0 + cols_per_chunk : n;
+        return c1 > c0 ? (int)((c1 - c0 + kBK - 1) / kBK) : 0;
+    };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < T::kStages; ++s) {
-            mbar_init(&ctl->full[s], 1);
-            mbar_init(&ctl->empty[s], 1);
-        }
-        mbar_init(&ctl->accum, 1);
-        fence_barrier_init();
+        init_ctl<PP, NA, MT>(ctl);
         prefetch_tmap(&tmX);
         if (NA == 2) prefetch_tmap(&tmXl);
         prefetch_tmap(&tmY);
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(&ctl->tmem, T::kTmemCols);
         tmem_relinquish();
     }
@@ -225,96 +282,131 @@ __global__ void __launch_bounds__(128, 1) xy_tc_kernel(const __grid_constant__ C
     const uint32_t tmem = ctl->tmem;
 
     if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % T::kStages;
-            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
-            if (!mbar_wait(&ctl->empty[st], ph ^ 1u)) {
-                atomicOr(err, kErrTimeout);
-                break;
-            }
-            uint8_t *a = smem + st * T::kStage;
-            const int col = (int)(c0 + (int64_t)kb * kBK);
-            mbar_expect_tx(&ctl->full[st], T::kStage);
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                // rows past dpad (an odd number of 128-row tiles) read as zeros
-                const int row = (int)r0 + mt * kBM;
-                uint8_t *am = a + mt * T::kA1;
-                tma_load_2d(am, &tmX, row, col, &ctl->full[st]);
-                tma_load_2d(am + kATile / 2, &tmX, row + 64, col, &ctl->full[st]);
-                if (NA == 2) {
-                    tma_load_2d(am + kATile, &tmXl, row, col, &ctl->full[st]);
-                    tma_load_2d(am + kATile + kATile / 2, &tmXl, row + 64, col, &ctl->full[st]);
+        int g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int rt = tile % rtiles, ch = tile / rtiles;
+            const int64_t r0 = (int64_t)rt * kBM * MT;
+            int64_t c0;
+            const int nkb = chunk_kb(ch, c0);
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int st = g % S;
+                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u)) {
+                    atomicOr(err, kErrTimeout);
+                    ok = false;
+                    break;
                 }
+                uint8_t *a = smem + st * T::kStage;
+                const int col = (int)(c0 + (int64_t)kb * kBK);
+                mbar_expect_tx(&ctl->full[st], T::kStage);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    // rows past dpad (an odd number of 128-row tiles) read as zeros
+                    const int row = (int)r0 + mt * kBM;
+                    uint8_t *am = a + mt * T::kA1;
+                    tma_load_2d(am, &tmX, row, col, &ctl->full[st]);
+                    tma_load_2d(am + kATile / 2, &tmX, row + 64, col, &ctl->full[st]);
+                    if (NA == 2) {
+                        tma_load_2d(am + kATile, &tmXl, row, col, &ctl->full[st]);
+                        tma_load_2d(am + kATile + kATile / 2, &tmXl, row + 64, col, &ctl->full[st]);
+                    }
+                }
+                tma_load_2d(a + T::kA, &tmY, col, 0, &ctl->full[st]);
+                tma_load_2d(a + T::kA + T::kB, &tmY, col, PP, &ctl->full[st]);
             }
-            tma_load_2d(a + T::kA, &tmY, col, 0, &ctl->full[st]);
-            tma_load_2d(a + T::kA + T::kB, &tmY, col, PP, &ctl->full[st]);
         }
+        if (!ok) drain_issued<S>(ctl, g);
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = instr_desc(1, 1, 0, PP, kBM);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % T::kStages;
-            const uint32_t ph = (uint32_t)(kb / T::kStages) & 1u;
-            if (!mbar_wait(&ctl->full[st], ph)) {
+        int g = 0, lt = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            int64_t c0;
+            const int nkb = chunk_kb(tile / rtiles, c0);
+            if (lt >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((lt >> 1) - 1) & 1u)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
             tc_fence_after();
-            const uint32_t a = smem_u32(smem + st * T::kStage);
-            const uint32_t bh = a + T::kA, bl = bh + T::kB;
+            const uint32_t accb = tmem + buf * T::kAccCols;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+                const int st = g % S;
+                if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u)) {
+                    atomicOr(err, kErrTimeout);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a = smem_u32(smem + st * T::kStage);
+                const uint32_t bh = a + T::kA, bl = bh + T::kB;
 #pragma unroll
-            for (int ks = 0; ks < kBK / 16; ++ks) {
-                const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+                for (int ks = 0; ks < kBK / 16; ++ks) {
+                    const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                    const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
-                    const uint32_t am = a + mt * T::kA1;
-                    const uint32_t acc = tmem + mt * kAccCols;
-                    const uint64_t ad = sw128_desc(am + ks * 2048, kATile / 2, 1024);
-                    mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
-                    mma_f16(acc, ad, bld, idesc, 1u);
-                    if (NA == 2)
-                        mma_f16(acc, sw128_desc(am + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                    for (int mt = 0; mt < MT; ++mt) {
+                        // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
+                        const uint32_t am = a + mt * T::kA1;
+                        const uint32_t acc = accb + mt * kAccCols1;
+                        const uint64_t ad = sw128_desc(am + ks * 2048, kATile / 2, 1024);
+                        mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
+                        mma_f16(acc, ad, bld, idesc, 1u);
+                        if (NA == 2)
+                            mma_f16(acc, sw128_desc(am + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                    }
+                }
+                mma_commit(&ctl->empty[st]);
+            }
+            if (ok) mma_commit(&ctl->accf[buf]);
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            const int rt = tile % rtiles, ch = tile / rtiles;
+            int64_t c0;
+            const int nkb = chunk_kb(ch, c0);
+            if (!mbar_wait(&ctl->accf[buf], (uint32_t)(lt >> 1) & 1u)) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const int64_t r0 = (int64_t)rt * kBM * MT;
+#pragma unroll 1
+            for (int mt = 0; mt < MT; ++mt) {
+                const int64_t r = r0 + mt * kBM + q * 32 + lane;
+                float *out = Gp + (int64_t)ch * dpad * PP + r * PP;
+                const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
+#pragma unroll
+                for (int c = 0; c < PP; c += 16) {
+                    float v[16];
+                    if (nkb > 0) {
+                        tmem_ld16(tl + c, v);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) v[u] = 0.0f;
+                    }
+                    if (r < dpad) {
+                        float4 *dst = reinterpret_cast<float4 *>(out + c);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                    }
                 }
             }
-            mma_commit(&ctl->empty[st]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->acce[buf]);
         }
-        mma_commit(&ctl->accum);
-    }
-    __syncwarp();
-
-    const bool ok = mbar_wait(&ctl->accum, 0);
-    tc_fence_after();
-    if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-    } else {
-#pragma unroll 1
-      for (int mt = 0; mt < MT; ++mt) {
-        const int64_t r = r0 + mt * kBM + warp * 32 + lane;
-        float *out = Gp + (int64_t)blockIdx.y * dpad * PP + r * PP;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + mt * kAccCols;
-#pragma unroll
-        for (int c = 0; c < PP; c += 16) {
-            float v[16];
-            if (nkb > 0) {
-                tmem_ld16(tl + c, v);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-            }
-            if (r < dpad) {
-                float4 *dst = reinterpret_cast<float4 *>(out + c);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
-        }
-      }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, T::kTmemCols);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, T::kTmemCols);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -396,6 +488,14 @@ CUtensorMap make_map(const void *base, uint64_t e0, uint64_t e1, uint64_t ld0, u
     return m;
 }
 
+// Streaming multiprocessors of the current device (one persistent CTA each).
+int sm_count() {
+    int dev = 0, v = 0;
+    LRA_CUDA(cudaGetDevice(&dev));
+    LRA_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v > 0 ? v : 1;
+}
+
 template <typename F>
 void dispatch_tc_pp(int PP, F &&f) {
     switch (PP) {
@@ -443,9 +543,10 @@ void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int
     const int rows = tc_rows_per_cta(PP, Xl != nullptr);
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, rows), sm_count());
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<(unsigned)ceil_div(n, rows), 128, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
+            kern<<<grid, kThreads, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
             LRA_LAUNCHED();
         };
         if (Xl)
@@ -466,10 +567,10 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
     const int rows = tc_rows_per_cta(PP, Xl != nullptr);
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
-        const dim3 grid((unsigned)ceil_div(dpad, rows), (unsigned)nchunks);
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(dpad, rows) * nchunks, sm_count());
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<grid, 128, smem, s>>>(mx, mxl, my, cpc, n, dpad, Gp, err);
+            kern<<<grid, kThreads, smem, s>>>(mx, mxl, my, cpc, nchunks, n, dpad, Gp, err);
             LRA_LAUNCHED();
         };
         if (Xl)
