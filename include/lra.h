@@ -92,6 +92,12 @@ typedef struct lra_options {
     int trace_cap;          /* length of trace_E */
     int profile;            /* 1: time the X-streaming and inner-loop kernels with CUDA events
                                on the launching stream (fills the *_ms / *_launches fields) */
+    int batch;              /* samples per SVRG inner step, 1..16 (default 1 = the step of
+                               Sec. 2.3).  b > 1 averages the stochastic term over b samples
+                               drawn at the same W (a minibatch, beyond the paper); the step
+                               size becomes theta_eta mu/(lambda^2 + kappa lambda1_up / b) and
+                               an epoch m = ceil(theta_m/(eta mu)) steps of b samples (at most
+                               m_max samples).  Must be a power of two. */
 } lra_options;
 
 typedef struct lra_report {
@@ -282,6 +288,16 @@ lra_status lra_x_mul(lra_mat *mat, int p, const float *Y, float *G, int use_f32_
  * The p columns are independent chains sharing the index sequence. */
 lra_status lra_svrg_inner(lra_mat *mat, int p, float *W, const float *Wt, const float *M,
                           const int32_t *idx, int64_t m, const float *c, double eta, double lambda);
+
+/* The same with a batch of `batch` samples per step (a power of two <= 16; the
+ * minibatch reading of lra_options.batch): idx holds m * batch entries, step t
+ * uses idx[t batch .. t batch + batch - 1], every r_u = x_{i_u}^T (W - Wt) is
+ * taken at the same W and W <- W - eta [lambda (W - Wt) - (1/batch) sum_u
+ * c[i_u] x_{i_u} r_u + M].  batch = 1 is lra_svrg_inner.  LRA_EUNSUPPORTED when
+ * the batch does not fit the dense kernel's shared-memory ring for this d. */
+lra_status lra_svrg_inner_batched(lra_mat *mat, int p, float *W, const float *Wt, const float *M,
+                                  const int32_t *idx, int64_t m, int batch, const float *c, double eta,
+                                  double lambda);
 
 typedef struct lra_solve_info {
     int epochs;            /* anchors computed */

@@ -166,6 +166,10 @@ def lra_svrg_inner(m, p, W, Wt, M, idx, steps, c, eta, lam) -> None:
     _check(lib.lra_svrg_inner(m, p, _p(W), _p(Wt), _p(M), _p(idx), steps, _p(c), eta, lam))
 
 
+def lra_svrg_inner_batched(m, p, W, Wt, M, idx, steps, batch, c, eta, lam) -> None:
+    _check(lib.lra_svrg_inner_batched(m, p, _p(W), _p(Wt), _p(M), _p(idx), steps, batch, _p(c), eta, lam))
+
+
 def lra_svrg_solve(m, p, B, W, lam, mu, lam1_up, seed, solve_id, opt=None):
     info = LraSolveInfo()
     st = _check(lib.lra_svrg_solve(m, p, _p(B), _p(W), lam, mu, lam1_up, seed, solve_id,

@@ -53,6 +53,7 @@ class LraOptions(C.Structure):
         ("trace_E", C.POINTER(C.c_double)),
         ("trace_cap", C.c_int),
         ("profile", C.c_int),
+        ("batch", C.c_int),
     ]
 
 
@@ -137,6 +138,7 @@ _PROTOS = {
     "lra_xt_mul": (ci, [vp, ci, vp, vp, ci]),
     "lra_x_mul": (ci, [vp, ci, vp, vp, ci]),
     "lra_svrg_inner": (ci, [vp, ci, vp, vp, vp, vp, i64, vp, dbl, dbl]),
+    "lra_svrg_inner_batched": (ci, [vp, ci, vp, vp, vp, vp, i64, ci, vp, dbl, dbl]),
     "lra_svrg_solve": (ci, [vp, ci, vp, vp, dbl, dbl, dbl, u64, i64, vp, vp]),
     "lra_gram": (ci, [vp, i64, ci, vp, i64, vp]),
     "lra_cholqr2": (ci, [vp, i64, ci, vp]),

@@ -130,6 +130,7 @@ void lra_options_default(lra_options *opt) {
     opt->sampling = LRA_SAMPLE_IMPORTANCE;
     opt->warm_start = 1;
     opt->max_shift_rounds = 30;
+    opt->batch = 1;
 }
 
 const char *lra_status_str(lra_status s) {
@@ -615,8 +616,16 @@ lra_status lra_x_mul(lra_mat *mat, int p, const float *Y, float *G, int use_f32_
 
 lra_status lra_svrg_inner(lra_mat *mat, int p, float *W, const float *Wt, const float *M,
                           const int32_t *idx, int64_t m, const float *c, double eta, double lambda) {
+    return lra_svrg_inner_batched(mat, p, W, Wt, M, idx, m, 1, c, eta, lambda);
+}
+
+lra_status lra_svrg_inner_batched(lra_mat *mat, int p, float *W, const float *Wt, const float *M,
+                                  const int32_t *idx, int64_t m, int batch, const float *c, double eta,
+                                  double lambda) {
     if (check_mat(mat) != LRA_OK || !W || !Wt || !M || (m > 0 && (!idx || !c))) return einval("null argument");
     if (p < 1 || p > LRA_MAX_P || m < 0) return einval("bad p or m");
+    if (batch < 1 || batch > 16 || (batch & (batch - 1)) != 0) return einval("batch must be a power of two <= 16");
+    const int64_t ns = m * batch;
     lra_ctx *ctx = mat->ctx;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     LRA_TRY({
@@ -628,10 +637,10 @@ lra_status lra_svrg_inner(lra_mat *mat, int p, float *W, const float *Wt, const 
         pt.upload(Wt, mat->d, mat->dpad, p);
         pm.upload(M, mat->d, mat->dpad, p);
         // cval[t] = c[idx[t]], the sampler's output convention
-        size_t cb = sizeof(float) * std::max<int64_t>(m, 1);
+        size_t cb = sizeof(float) * std::max<int64_t>(ns, 1);
         float *cval = static_cast<float *>(dev_alloc(ctx, cb));
         try {
-            gather_c(ctx->stream, idx, c, m, mat->n, cval, ws.status);
+            gather_c(ctx->stream, idx, c, ns, mat->n, cval, ws.status);
             int bad = 0;
             LRA_CUDA(cudaMemcpyAsync(&bad, ws.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
             LRA_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -639,7 +648,7 @@ lra_status lra_svrg_inner(lra_mat *mat, int p, float *W, const float *Wt, const 
                 set_error("index out of range");
                 throw Error{LRA_EINVAL};
             }
-            e.inner(pw.p, pt.p, pm.p, p, idx, cval, m, eta, lambda);
+            e.inner(pw.p, pt.p, pm.p, p, idx, cval, m, eta, lambda, batch);
             pw.download(W, mat->d, mat->dpad, p);
             LRA_CUDA(cudaStreamSynchronize(ctx->stream));
         } catch (...) {

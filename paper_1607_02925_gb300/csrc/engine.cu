@@ -67,11 +67,13 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
         r.trace_E = o->trace_E;
         r.trace_cap = o->trace_cap;
         r.profile = o->profile;
+        r.batch = o->batch;
     }
     if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
     if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
         r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
-        r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0)) {
+        r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0) || r.batch < 1 || r.batch > 16 ||
+        (r.batch & (r.batch - 1)) != 0) {
         set_error("invalid lra_options field");
         throw Error{LRA_EINVAL};
     }
@@ -402,7 +404,7 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
 }
 
 void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
-                   const float *cval, int64_t m, double eta, double lam) {
+                   const float *cval, int64_t m, double eta, double lam, int batch) {
     if (mat_->sp) {
         // factored form: Mr = M row-major in Wr, Z in the G buffer (both free
         // between the anchor's epilogue and the next X pass)
@@ -410,13 +412,13 @@ void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32
         pack_rm(s_, M, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
         if (timer) timer->begin(KernelTimer::INNER, p);
         svrg_inner_csc(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->dpad, p, PP, W, Wt, ws_.Wr,
-                       ws_.Gp, ws_.dots, idx, cval, m, eta, lam);
+                       ws_.Gp, ws_.dots, idx, cval, m, eta, lam, batch);
         if (timer) timer->end();
         return;
     }
     if (timer) timer->begin(KernelTimer::INNER, p);
     svrg_inner(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, p, W, Wt, M, idx, cval, m,
-               (float)eta, (float)lam);
+               (float)eta, (float)lam, batch);
     if (timer) timer->end();
 }
 
@@ -496,9 +498,11 @@ double Engine::dot1(const float *a, const float *b) {
 
 void Engine::step_params(double lam, double mu, double l1up, double kappa, const Opts &o,
                          double &eta, int64_t &m) const {
-    eta = o.theta_eta * mu / (lam * lam + kappa * l1up);
+    // a batch of b samples divides the variance term kappa lambda1_up by b
+    const int b = o.batch;
+    eta = o.theta_eta * mu / (lam * lam + kappa * l1up / b);
     const double mm = std::ceil(o.theta_m / (eta * mu));
-    const int64_t m_max = o.m_max > 0 ? o.m_max : 50 * mat_->n;
+    const int64_t m_max = std::max<int64_t>(1, (o.m_max > 0 ? o.m_max : 50 * mat_->n) / b);
     m = (mm > (double)m_max) ? m_max : (int64_t)mm;
 }
 
@@ -538,10 +542,11 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
         }
         best = std::min(best, res);
         prev = res;
-        ws_.ensure_idx(m);
+        const int64_t ns = m * o.batch;  // samples of the epoch
+        ws_.ensure_idx(ns);
         const uint64_t key = stream_key(seed, LRA_STREAM_SVRG, (uint64_t)solve_id, (uint64_t)e);
-        sample(s_, tab.cum, mat_->n, key, m, ws_.idx, tab.c, ws_.cval);
-        inner(W, ws_.Wt, ws_.M, p, ws_.idx, ws_.cval, m, eta, lam);
+        sample(s_, tab.cum, mat_->n, key, ns, ws_.idx, tab.c, ws_.cval);
+        inner(W, ws_.Wt, ws_.M, p, ws_.idx, ws_.cval, m, eta, lam, o.batch);
         info.inner_steps += m;
         stats.inner_steps += m;
     }

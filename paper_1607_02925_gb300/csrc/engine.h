@@ -80,6 +80,7 @@ struct Opts {
     double *trace_E = nullptr;
     int trace_cap = 0;
     int profile = 0;
+    int batch = 1;
 };
 
 // CUDA-event timing of individual kernel launches on the engine's stream.
@@ -187,8 +188,9 @@ class Engine {
     // G0 != nullptr: X X^T Wt precomputed (dpad x PP row-major), no X pass
     void anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
                 double *nM2, double *nB2);
+    // m steps of `batch` samples (idx / cval hold m * batch entries)
     void inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
-               const float *cval, int64_t m, double eta, double lam);
+               const float *cval, int64_t m, double eta, double lam, int batch = 1);
     // deferred: enqueue the status read-back without waiting (check with qr_status()
     // after the next synchronisation of the stream)
     lra_status cholqr2(float *W, int p, bool deferred = false);

@@ -1,5 +1,6 @@
 // SVRG inner loop (Sec. 2.3, SVRGsolve): m serial variance-reduced steps
 //   r = x_i^T (W - Wt),  W <- W - eta [lambda (W - Wt) - c_i x_i r + M]
+// (or, with a batch of b samples, the stochastic term averaged over b)
 // on the p columns of W, which are independent chains sharing the sampled
 // index sequence.  One CTA owns PC columns and the whole d-long state of each:
 // the difference Delta = W - Wt and the anchor gradient M live in registers,
@@ -9,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <string>
 
 #include "kernels.cuh"
 
@@ -31,19 +33,24 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Thread t owns rows 4 (t + s NT) + v for s < S, v < 4 (rows >= dpad skipped).
-template <typename TX, int S, int PC>
+// A step takes NB samples (NB = 1: Sec. 2.3's step; NB = batch b > 1: the
+// stochastic term averaged over b samples at the same W).  The ring holds D
+// steps of NB columns, D - 1 steps fetched ahead; each thread copies and reads
+// only its own rows of a column, so the ring needs no barrier.
+template <typename TX, int S, int PC, int MB, int D>
 __global__ void __launch_bounds__(512) svrg_inner_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, int nb, float eta, float lam) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [kRing][dpad]
-    __shared__ float red[2][16][PC];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [D * nb][dpad]
+    __shared__ float red[2][16][MB * PC];
 
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
     const int j0 = blockIdx.x * PC;
+    const int nslot = D * nb;  // a power of two
     constexpr int BYTES = 4 * sizeof(TX);
 
     float dl[S][4][PC];   // Delta = W - Wt
@@ -65,28 +72,21 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
 
     auto prefetch = [&](int64_t t) {
         if (t < m) {
-            const int64_t i = idx[t];
-            const TX *col = X + i * ldx;
-            TX *slot = ring + (t & (kRing - 1)) * dpad;
+            for (int u = 0; u < nb; ++u) {
+                const int64_t smp = t * nb + u;
+                const TX *col = X + (int64_t)idx[smp] * ldx;
+                TX *slot = ring + (smp & (nslot - 1)) * dpad;
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
-                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+                for (int s = 0; s < S; ++s) {
+                    const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+                    if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+                }
             }
         }
         cp_async_commit();
     };
-
-    prefetch(0);
-    prefetch(1);
-    prefetch(2);
-    const float a = 1.0f - eta * lam;
-
-    for (int64_t t = 0; t < m; ++t) {
-        prefetch(t + 3);
-        cp_async_wait<3>();
-        const TX *slot = ring + (t & (kRing - 1)) * dpad;
-        float x[S][4];
+    auto load_x = [&](int64_t smp, float (&x)[S][4]) {
+        const TX *slot = ring + (smp & (nslot - 1)) * dpad;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
@@ -105,37 +105,120 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
                 for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
             }
         }
-        const float ci = cval[t];
-        float part[PC];
+    };
+
 #pragma unroll
-        for (int j = 0; j < PC; ++j) {
-            float acc = 0.0f;
+    for (int q = 0; q < D - 1; ++q) prefetch(q);
+    const float a = 1.0f - eta * lam;
+    const float invb = 1.0f / (float)nb;
+
+    for (int64_t t = 0; t < m; ++t) {
+        prefetch(t + D - 1);
+        cp_async_wait<D - 1>();
+        if constexpr (MB == 1) {
+            // one sample: x stays in registers between the dot product and the update
+            float x[S][4];
+            load_x(t, x);
+            const float ci = cval[t];
+            float part[PC];
+#pragma unroll
+            for (int j = 0; j < PC; ++j) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
+                part[j] = warp_sum(acc);
+            }
+            const int buf = (int)(t & 1);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
+            }
+            __syncthreads();
+            float coef[PC];
+#pragma unroll
+            for (int j = 0; j < PC; ++j) {
+                float rj = 0.0f;
+                for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
+                coef[j] = eta * ci * rj;
+            }
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
-            part[j] = warp_sum(acc);
+                for (int v = 0; v < 4; ++v)
+#pragma unroll
+                    for (int j = 0; j < PC; ++j)
+                        dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(coef[j], x[s][v], -mm[s][v][j]));
+        } else {
+        // r_u = x_u^T Delta for every sample of the step (same Delta)
+        float part[MB][PC];
+#pragma unroll
+        for (int u = 0; u < MB; ++u) {
+            if (u < nb) {
+                float x[S][4];
+                load_x(t * nb + u, x);
+#pragma unroll
+                for (int j = 0; j < PC; ++j) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
+                    part[u][j] = warp_sum(acc);
+                }
+            }
         }
         const int buf = (int)(t & 1);
         if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
+            for (int u = 0; u < MB; ++u)
+                if (u < nb)
+#pragma unroll
+                    for (int j = 0; j < PC; ++j) red[buf][warp][u * PC + j] = part[u][j];
         }
         __syncthreads();
-        float coef[PC];
+        float coef[MB][PC];
 #pragma unroll
-        for (int j = 0; j < PC; ++j) {
-            float rj = 0.0f;
-            for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
-            coef[j] = eta * ci * rj;
+        for (int u = 0; u < MB; ++u) {
+            if (u < nb) {
+                const float cu = cval[t * nb + u];
+#pragma unroll
+                for (int j = 0; j < PC; ++j) {
+                    float rj = 0.0f;
+                    for (int w = 0; w < nwarps; ++w) rj += red[buf][w][u * PC + j];
+                    coef[u][j] = eta * cu * rj * invb;
+                }
+            }
+        }
+        // Delta <- a Delta + sum_u coef_u x_u - eta M
+        float upd[S][4][PC];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int j = 0; j < PC; ++j) upd[s][v][j] = -mm[s][v][j];
+#pragma unroll
+        for (int u = 0; u < MB; ++u) {
+            if (u < nb) {
+                float x[S][4];
+                load_x(t * nb + u, x);
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int j = 0; j < PC; ++j) upd[s][v][j] = fmaf(coef[u][j], x[s][v], upd[s][v][j]);
+            }
         }
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int v = 0; v < 4; ++v)
 #pragma unroll
-                for (int j = 0; j < PC; ++j)
-                    dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(coef[j], x[s][v], -mm[s][v][j]));
+                for (int j = 0; j < PC; ++j) dl[s][v][j] = fmaf(a, dl[s][v][j], upd[s][v][j]);
+        }
     }
     cp_async_wait<0>();
 
@@ -153,61 +236,87 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
     }
 }
 
-template <typename TX, int S, int PC>
+template <typename TX, int S, int PC, int MB, int D>
 void launch_inner(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                   const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                  float eta, float lam, int nt) {
-    auto k = svrg_inner_kernel<TX, S, PC>;
-    const size_t smem = (size_t)kRing * dpad * sizeof(TX);
+                  int nb, float eta, float lam, int nt) {
+    auto k = svrg_inner_kernel<TX, S, PC, MB, D>;
+    const size_t smem = (size_t)D * nb * dpad * sizeof(TX);
     ensure_smem(k, (int)smem);
     const unsigned grid = (unsigned)ceil_div(p, PC);
-    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, nb, eta, lam);
     LRA_LAUNCHED();
 }
 
 template <typename TX>
 constexpr size_t dt_size() { return sizeof(TX); }
 
+constexpr size_t kRingBytes = 220 * 1024;
+
 template <typename TX>
 void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                     const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                    float eta, float lam) {
+                    int nb, float eta, float lam) {
     // threads: 4 rows each, at most 512; S = row groups per thread
     const int64_t groups = dpad / 4;
     int nt = (int)std::min<int64_t>(512, round_up(groups, 32));
-    const int64_t S = ceil_div(groups, nt);
-    // columns per CTA: keep about <= 64 CTAs streaming the same x_i, and the
-    // register state (8 S PC floats) within 64 registers
-    const int pc = (p <= 64 || S > 4) ? 1 : 2;
-    if ((size_t)kRing * dpad * (dt_size<TX>()) > 220 * 1024) {
-        set_error("dense inner loop: d too large for the shared-memory ring");
+    int64_t S = ceil_div(groups, nt);
+    if (S > 8) {
+        set_error("dense inner loop supports d <= 16384");
         throw Error{LRA_EUNSUPPORTED};
     }
-#define LRA_INNER_CASE(SS, PCC)                                                                 \
-    if (S == SS && pc == PCC) {                                                                 \
-        launch_inner<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt); \
-        return;                                                                                 \
+    if (nb == 1) {
+        // columns per CTA: keep about <= 64 CTAs streaming the same x_i, and the
+        // register state (8 S PC floats) within 64 registers
+        const int pc = (p <= 64 || S > 4) ? 1 : 2;
+        if ((size_t)kRing * dpad * (dt_size<TX>()) > kRingBytes) {
+            set_error("dense inner loop: d too large for the shared-memory ring");
+            throw Error{LRA_EUNSUPPORTED};
+        }
+        if (S == 5) S = 6;
+        if (S == 7) S = 8;
+#define LRA_INNER_CASE(SS, PCC)                                                                             \
+    if (S == SS && pc == PCC) {                                                                             \
+        launch_inner<TX, SS, PCC, 1, kRing>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, 1, eta, lam, nt); \
+        return;                                                                                             \
     }
-    LRA_INNER_CASE(1, 1)
-    LRA_INNER_CASE(1, 2)
-    LRA_INNER_CASE(2, 1)
-    LRA_INNER_CASE(2, 2)
-    LRA_INNER_CASE(3, 1)
-    LRA_INNER_CASE(3, 2)
-    LRA_INNER_CASE(4, 1)
-    LRA_INNER_CASE(4, 2)
-    LRA_INNER_CASE(6, 1)
-    LRA_INNER_CASE(8, 1)
+        LRA_INNER_CASE(1, 1)
+        LRA_INNER_CASE(1, 2)
+        LRA_INNER_CASE(2, 1)
+        LRA_INNER_CASE(2, 2)
+        LRA_INNER_CASE(3, 1)
+        LRA_INNER_CASE(3, 2)
+        LRA_INNER_CASE(4, 1)
+        LRA_INNER_CASE(4, 2)
+        LRA_INNER_CASE(6, 1)
+        LRA_INNER_CASE(8, 1)
 #undef LRA_INNER_CASE
-    if (S <= 8) {
-        // S in {5, 7}: round up to the next instantiated size
-        if (S <= 6)
-            launch_inner<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
-        else
-            launch_inner<TX, 8, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
-        return;
+    } else {
+        // a batch: one column per CTA, two steps of nb columns in the ring
+        if ((size_t)2 * nb * dpad * (dt_size<TX>()) > kRingBytes) {
+            set_error("dense inner loop: batch too large for d (the ring holds 2 b columns of X)");
+            throw Error{LRA_EUNSUPPORTED};
+        }
+        if (S == 3) S = 4;
+        if (S > 4) S = 8;
+        // registers hold MB partial sums per step: 16 for d <= 2048, fewer above
+        const int mb = S <= 2 ? 16 : (S == 4 ? 8 : 2);
+        if (nb > mb) {
+            set_error("dense inner loop: batch too large for d (at most " + std::to_string(mb) + ")");
+            throw Error{LRA_EUNSUPPORTED};
+        }
+#define LRA_INNER_BCASE(SS, MBB)                                                                            \
+    if (S == SS) {                                                                                          \
+        launch_inner<TX, SS, 1, MBB, 2>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, nb, eta, lam, nt);    \
+        return;                                                                                             \
     }
-    set_error("dense inner loop supports d <= 16384");
+        LRA_INNER_BCASE(1, 16)
+        LRA_INNER_BCASE(2, 16)
+        LRA_INNER_BCASE(4, 8)
+        LRA_INNER_BCASE(8, 2)
+#undef LRA_INNER_BCASE
+    }
+    set_error("dense inner loop: no kernel for this shape");
     throw Error{LRA_EUNSUPPORTED};
 }
 
@@ -215,12 +324,16 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
 
 void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
                 float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
-                int64_t m, float eta, float lam) {
+                int64_t m, float eta, float lam, int batch) {
     if (m <= 0) return;  // an empty step sequence leaves W unchanged
+    if (batch < 1 || batch > 16 || (batch & (batch - 1)) != 0) {
+        set_error("batch must be a power of two in [1, 16]");
+        throw Error{LRA_EINVAL};
+    }
     if (dt == LRA_BF16)
-        inner_dispatch<__nv_bfloat16>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+        inner_dispatch<__nv_bfloat16>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam);
     else
-        inner_dispatch<float>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+        inner_dispatch<float>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam);
 }
 
 }  // namespace lra

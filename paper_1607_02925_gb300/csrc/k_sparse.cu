@@ -553,6 +553,75 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
     }
 }
 
+// The same chain with a batch of nb > 1 samples per step (stochastic term
+// averaged, every r_u taken at the same W): warp w computes r_u for the
+// columns u = w, w + 8, ... (a whole column each, entries in order); the
+// updates of the nb columns then go in turn (columns of a batch may share
+// rows), each split over the warps.
+template <int NQ>
+__global__ void __launch_bounds__(32 * kWarps) inner_csc_batch_kernel(
+    const int64_t *__restrict__ colptr, const int32_t *__restrict__ rowidx, const float *__restrict__ cval,
+    int64_t dpad, int PP, const float *__restrict__ Mr, float *__restrict__ Z, const int32_t *__restrict__ idx,
+    const float *__restrict__ cvals, int64_t m, int nb, double eta, double lam, double *__restrict__ ab) {
+    __shared__ float rv[16][32 * NQ];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const double g = 1.0 - eta * lam;
+    double a = 1.0, b = 0.0;
+    for (int64_t t = 0; t < m; ++t) {
+        for (int u = w; u < nb; u += kWarps) {
+            const int64_t i = idx[t * nb + u];
+            const int64_t lo = colptr[i], hi = colptr[i + 1];
+            float sz[NQ], sm[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sz[q] = sm[q] = 0.0f;
+#pragma unroll 4
+            for (int64_t k = lo; k < hi; ++k) {
+                const int64_t r = rowidx[k];
+                const float v = cval[k];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < PP) {
+                        sz[q] = fmaf(v, Z[r * PP + j], sz[q]);
+                        sm[q] = fmaf(v, __ldg(Mr + r * PP + j), sm[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) rv[u][lane + 32 * q] = (float)(a * (double)sz[q] + b * (double)sm[q]);
+        }
+        __syncthreads();
+        const double a1 = g * a;
+        b = g * b - eta;
+        for (int u = 0; u < nb; ++u) {
+            const int64_t i = idx[t * nb + u];
+            const int64_t lo = colptr[i], hi = colptr[i + 1];
+            const float coef = (float)(eta * (double)cvals[t * nb + u] / (a1 * (double)nb));
+            for (int64_t k = lo + w; k < hi; k += kWarps) {
+                const int64_t r = rowidx[k];
+                const float cv = coef * cval[k];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < PP) Z[r * PP + j] = fmaf(cv, rv[u][j], Z[r * PP + j]);
+                }
+            }
+            __syncthreads();
+        }
+        a = a1;
+        if (a < 0x1p-30) {
+            const float af = (float)a;
+            for (int64_t e = tid; e < dpad * PP; e += blockDim.x) Z[e] *= af;
+            a = 1.0;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        ab[0] = a;
+        ab[1] = b;
+    }
+}
+
 __global__ void inner_final_kernel(const float *__restrict__ Wt, const float *__restrict__ Z,
                                    const float *__restrict__ Mr, const double *__restrict__ ab, int64_t dpad, int p,
                                    int PP, float *__restrict__ W) {
@@ -653,14 +722,22 @@ void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const 
 
 void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
                     int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
-                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam) {
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch) {
     if (m <= 0) return;
+    if (batch < 1 || batch > 16) {
+        set_error("batch must be in [1, 16]");
+        throw Error{LRA_EINVAL};
+    }
     zdiff_kernel<<<grid_for(dpad * PP, 256), 256, 0, s>>>(W, Wt, dpad, p, PP, Z);
     LRA_LAUNCHED();
     dispatch_nq(PP, [&](auto nq) {
         constexpr int NQ = decltype(nq)::value;
-        inner_csc_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, eta, lam,
-                                                       ab);
+        if (batch == 1)
+            inner_csc_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, eta,
+                                                           lam, ab);
+        else
+            inner_csc_batch_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m,
+                                                                 batch, eta, lam, ab);
         LRA_LAUNCHED();
     });
     inner_final_kernel<<<grid_for(dpad * p, 256), 256, 0, s>>>(Wt, Z, Mr, ab, dpad, p, PP, W);

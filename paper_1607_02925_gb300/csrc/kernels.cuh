@@ -72,9 +72,10 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
            const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err);
 
 // ---- SVRG inner loop (k_inner.cu) -----------------------------------------
+// m steps of `batch` samples each (idx, cval: m * batch entries); batch a power of two <= 16
 void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
                 float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
-                int64_t m, float eta, float lam);
+                int64_t m, float eta, float lam, int batch = 1);
 
 // ---- p x p and d x p helpers (k_small.cu) -------------------------------
 // G (p x p FP64, column-major) = A^T A, A rows x p with strides (rs, cs).
@@ -160,6 +161,6 @@ void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const 
 // Mr = M packed dpad x PP row-major; Z: dpad x PP scratch; ab: 2 doubles
 void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
                     int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
-                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam);
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch = 1);
 
 }  // namespace lra
