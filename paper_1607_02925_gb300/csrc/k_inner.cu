@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 
 #include "kernels.cuh"
@@ -32,25 +33,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Thread t owns rows 4 (t + s NT) + v for s < S, v < 4 (rows >= dpad skipped).
-// A step takes NB samples (NB = 1: Sec. 2.3's step; NB = batch b > 1: the
-// stochastic term averaged over b samples at the same W).  The ring holds D
-// steps of NB columns, D - 1 steps fetched ahead; each thread copies and reads
-// only its own rows of a column, so the ring needs no barrier.
-template <typename TX, int S, int PC, int MB, int D>
-__global__ void __launch_bounds__(512) svrg_inner_kernel(
+// One sample per step.  Thread t owns rows 4 (t + s NT) + v for s < S, v < 4
+// (rows >= dpad skipped).
+template <typename TX, int S, int PC>
+__global__ void __launch_bounds__(512) svrg_inner1_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, int nb, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, float eta, float lam) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [D * nb][dpad]
-    __shared__ float red[2][16][MB * PC];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [kRing][dpad]
+    __shared__ float red[2][16][PC];
 
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
     const int j0 = blockIdx.x * PC;
-    const int nslot = D * nb;  // a power of two
     constexpr int BYTES = 4 * sizeof(TX);
 
     float dl[S][4][PC];   // Delta = W - Wt
@@ -72,8 +69,137 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
 
     auto prefetch = [&](int64_t t) {
         if (t < m) {
-            for (int u = 0; u < nb; ++u) {
-                const int64_t smp = t * nb + u;
+            const int64_t i = idx[t];
+            const TX *col = X + i * ldx;
+            TX *slot = ring + (t & (kRing - 1)) * dpad;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+            }
+        }
+        cp_async_commit();
+    };
+
+    prefetch(0);
+    prefetch(1);
+    prefetch(2);
+    const float a = 1.0f - eta * lam;
+
+    for (int64_t t = 0; t < m; ++t) {
+        prefetch(t + 3);
+        cp_async_wait<3>();
+        const TX *slot = ring + (t & (kRing - 1)) * dpad;
+        float x[S][4];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+            if (r < dpad) {
+                if constexpr (sizeof(TX) == 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
+                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
+                } else {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
+            }
+        }
+        const float ci = cval[t];
+        float part[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
+            part[j] = warp_sum(acc);
+        }
+        const int buf = (int)(t & 1);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
+        }
+        __syncthreads();
+        float coef[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float rj = 0.0f;
+            for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
+            coef[j] = eta * ci * rj;
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int j = 0; j < PC; ++j)
+                    dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(coef[j], x[s][v], -mm[s][v][j]));
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            if (r < dpad && j0 + j < p) {
+                const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) W[off + v] = Wt[off + v] + dl[s][v][j];
+            }
+        }
+    }
+}
+
+// A batch of NB > 1 samples per step: the stochastic term averaged over the
+// NB samples, every r_u taken at the same W.  One column per CTA; the ring
+// holds D steps of NB columns, D - 1 steps fetched ahead; each thread copies
+// and reads only its own rows of a column, so the ring needs no barrier.
+template <typename TX, int S, int NB, int D>
+__global__ void __launch_bounds__(512) svrg_inner_batch_kernel(
+    const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
+    const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
+    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    constexpr int PC = 1, MB = NB, nb = NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [D * NB][dpad]
+    __shared__ float red[2][16][NB];
+
+    const int tid = threadIdx.x;
+    const int NT = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+    const int j0 = blockIdx.x * PC;
+    constexpr int nslot = D * NB;  // a power of two
+    constexpr int BYTES = 4 * sizeof(TX);
+
+    float dl[S][4][PC];   // Delta = W - Wt
+    float mm[S][4][PC];   // eta * M
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            const bool ok = (r < dpad) && (j0 + j < p);
+            const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                dl[s][v][j] = ok ? (W[off + v] - Wt[off + v]) : 0.0f;
+                mm[s][v][j] = ok ? eta * M[off + v] : 0.0f;
+            }
+        }
+    }
+
+    auto prefetch = [&](int64_t t) {
+        if (t < m) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int64_t smp = t * NB + u;
                 const TX *col = X + (int64_t)idx[smp] * ldx;
                 TX *slot = ring + (smp & (nslot - 1)) * dpad;
 #pragma unroll
@@ -115,42 +241,7 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
     for (int64_t t = 0; t < m; ++t) {
         prefetch(t + D - 1);
         cp_async_wait<D - 1>();
-        if constexpr (MB == 1) {
-            // one sample: x stays in registers between the dot product and the update
-            float x[S][4];
-            load_x(t, x);
-            const float ci = cval[t];
-            float part[PC];
-#pragma unroll
-            for (int j = 0; j < PC; ++j) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int s = 0; s < S; ++s)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
-                part[j] = warp_sum(acc);
-            }
-            const int buf = (int)(t & 1);
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
-            }
-            __syncthreads();
-            float coef[PC];
-#pragma unroll
-            for (int j = 0; j < PC; ++j) {
-                float rj = 0.0f;
-                for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
-                coef[j] = eta * ci * rj;
-            }
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-#pragma unroll
-                    for (int j = 0; j < PC; ++j)
-                        dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(coef[j], x[s][v], -mm[s][v][j]));
-        } else {
+        {
         // r_u = x_u^T Delta for every sample of the step (same Delta)
         float part[MB][PC];
 #pragma unroll
@@ -236,15 +327,26 @@ __global__ void __launch_bounds__(512) svrg_inner_kernel(
     }
 }
 
-template <typename TX, int S, int PC, int MB, int D>
-void launch_inner(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
-                  const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                  int nb, float eta, float lam, int nt) {
-    auto k = svrg_inner_kernel<TX, S, PC, MB, D>;
-    const size_t smem = (size_t)D * nb * dpad * sizeof(TX);
+template <typename TX, int S, int PC>
+void launch_inner1(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
+                   const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
+                   float eta, float lam, int nt) {
+    auto k = svrg_inner1_kernel<TX, S, PC>;
+    const size_t smem = (size_t)kRing * dpad * sizeof(TX);
     ensure_smem(k, (int)smem);
     const unsigned grid = (unsigned)ceil_div(p, PC);
-    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, nb, eta, lam);
+    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    LRA_LAUNCHED();
+}
+
+template <typename TX, int S, int NB, int D>
+void launch_batch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
+                  const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
+                  float eta, float lam, int nt) {
+    auto k = svrg_inner_batch_kernel<TX, S, NB, D>;
+    const size_t smem = (size_t)D * NB * dpad * sizeof(TX);
+    ensure_smem(k, (int)smem);
+    k<<<(unsigned)p, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
     LRA_LAUNCHED();
 }
 
@@ -273,12 +375,10 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
             set_error("dense inner loop: d too large for the shared-memory ring");
             throw Error{LRA_EUNSUPPORTED};
         }
-        if (S == 5) S = 6;
-        if (S == 7) S = 8;
-#define LRA_INNER_CASE(SS, PCC)                                                                             \
-    if (S == SS && pc == PCC) {                                                                             \
-        launch_inner<TX, SS, PCC, 1, kRing>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, 1, eta, lam, nt); \
-        return;                                                                                             \
+#define LRA_INNER_CASE(SS, PCC)                                                                     \
+    if (S == SS && pc == PCC) {                                                                     \
+        launch_inner1<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);     \
+        return;                                                                                     \
     }
         LRA_INNER_CASE(1, 1)
         LRA_INNER_CASE(1, 2)
@@ -291,33 +391,59 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
         LRA_INNER_CASE(6, 1)
         LRA_INNER_CASE(8, 1)
 #undef LRA_INNER_CASE
-    } else {
-        // a batch: one column per CTA, two steps of nb columns in the ring
-        if ((size_t)2 * nb * dpad * (dt_size<TX>()) > kRingBytes) {
-            set_error("dense inner loop: batch too large for d (the ring holds 2 b columns of X)");
-            throw Error{LRA_EUNSUPPORTED};
+        if (S <= 6) {
+            launch_inner1<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+        } else {
+            launch_inner1<TX, 8, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
         }
-        if (S == 3) S = 4;
-        if (S > 4) S = 8;
-        // registers hold MB partial sums per step: 16 for d <= 2048, fewer above
-        const int mb = S <= 2 ? 16 : (S == 4 ? 8 : 2);
-        if (nb > mb) {
-            set_error("dense inner loop: batch too large for d (at most " + std::to_string(mb) + ")");
-            throw Error{LRA_EUNSUPPORTED};
+        return;
+    }
+    // a batch: one column per CTA; the ring holds four steps of nb columns when
+    // it fits (three steps fetched ahead), else two
+    const size_t col = (size_t)dpad * dt_size<TX>();
+    const int depth = (size_t)4 * nb * col <= kRingBytes ? 4 : ((size_t)2 * nb * col <= kRingBytes ? 2 : 0);
+    if (depth == 0) {
+        set_error("dense inner loop: batch too large for d (the ring holds 2 b columns of X)");
+        throw Error{LRA_EUNSUPPORTED};
+    }
+    if (S > 2 && nb > 8) {
+        set_error("dense inner loop: batch 16 needs d <= 2048");
+        throw Error{LRA_EUNSUPPORTED};
+    }
+    if (S == 3) S = 4;
+    if (S > 4) S = 8;
+    if (S == 8 && nb > 2) {
+        set_error("dense inner loop: batch above 2 needs d <= 8192");
+        throw Error{LRA_EUNSUPPORTED};
+    }
+    auto go = [&](auto sc, auto nbc) {
+        constexpr int SS = decltype(sc)::value, NBB = decltype(nbc)::value;
+        if (depth == 4)
+            launch_batch<TX, SS, NBB, 4>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+        else
+            launch_batch<TX, SS, NBB, 2>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+    };
+    using std::integral_constant;
+    auto by_nb = [&](auto sc) {
+        switch (nb) {
+            case 2: go(sc, integral_constant<int, 2>{}); break;
+            case 4: go(sc, integral_constant<int, 4>{}); break;
+            case 8: go(sc, integral_constant<int, 8>{}); break;
+            default: go(sc, integral_constant<int, 16>{}); break;
         }
-#define LRA_INNER_BCASE(SS, MBB)                                                                            \
-    if (S == SS) {                                                                                          \
-        launch_inner<TX, SS, 1, MBB, 2>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, nb, eta, lam, nt);    \
-        return;                                                                                             \
+    };
+    switch (S) {
+        case 1: by_nb(integral_constant<int, 1>{}); break;
+        case 2: by_nb(integral_constant<int, 2>{}); break;
+        case 4:
+            if (nb <= 8) {
+                if (nb == 2) go(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+                else if (nb == 4) go(integral_constant<int, 4>{}, integral_constant<int, 4>{});
+                else go(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+            }
+            break;
+        default: go(integral_constant<int, 8>{}, integral_constant<int, 2>{}); break;
     }
-        LRA_INNER_BCASE(1, 16)
-        LRA_INNER_BCASE(2, 16)
-        LRA_INNER_BCASE(4, 8)
-        LRA_INNER_BCASE(8, 2)
-#undef LRA_INNER_BCASE
-    }
-    set_error("dense inner loop: no kernel for this shape");
-    throw Error{LRA_EUNSUPPORTED};
 }
 
 }  // namespace
