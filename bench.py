@@ -494,6 +494,11 @@ def run_lra(args):
             if kk in cols:
                 pav = cols[kk] / cnt[kk]
                 e["x_pass_gbs"] = src.pass_bytes(kk, pav) / (tot[kk] / cnt[kk] / 1e3) / 1e9
+            if kk == "inner":
+                steps = sum(r.inner_steps for _, r in reps)
+                if steps > 0:
+                    e["steps"] = steps
+                    e["ns_per_step"] = tot[kk] * 1e6 / steps
             per_kernel[kk] = e
 
     # end to end through the C ABI with host buffers
@@ -649,7 +654,8 @@ def run_serve(args):
     lat = np.array(done_t) - arrivals
     span = max(done_t) - arrivals[0]
     # sampled results re-run alone must be bitwise equal
-    check = list(range(0, nreq, max(1, nreq // 10)))[:10]
+    nchk = min(50, nreq)
+    check = list(range(0, nreq, max(1, nreq // nchk)))[:nchk]
     equal = 0
     for j in check:
         q = reqs[j]
