@@ -334,6 +334,10 @@ class Options:
     warm_start: int = 1
     max_shift_rounds: int = 30
     batch: int = 1              # samples per inner step (minibatch reading; 1 = Sec. 2.3)
+    acc: int = 0                # 1: accelerated SVRG (AccSVRGsolve reading, acc_svrg_solve)
+    acc_theta: float = 0.5      # inner accuracy: ||grad|| <= max(tau ||B||, theta sqrt(q) ||r_s||)
+    acc_max_outer: int = 200    # proximal-point iterations per accelerated solve
+    acc_target: int = 0         # samples per epoch the proximal term aims for; 0 = n
 
 
 @dataclass
@@ -342,6 +346,22 @@ class SolveStats:
     inner_steps: int = 0
     residual: float = float("nan")
     status: str = "ok"            # ok | notconv | diverged
+    outer: int = 0                # proximal-point iterations (accelerated solves)
+    outer_res: float = float("nan")  # ||(lambda I - A) W - B|| at the epoch-0 anchor (accelerated)
+    outer_done: bool = False
+
+
+@dataclass
+class AccStep:
+    """One proximal subproblem of the accelerated solve: the epoch-0 anchor of
+    the inner solve also yields the residual of the original system,
+    (lambda I - A) W - B = M' - gamma (W - Z), where M' is that anchor's
+    gradient of the subproblem.  The inner solve stops at ||M'|| <= tol (set
+    from that residual) instead of at tau ||R||."""
+    gamma: float
+    Z: np.ndarray
+    nB: float                     # ||B||_F of the original system
+    sq: float                     # sqrt(q), q = mu / (mu + gamma)
 
 
 class Context:
@@ -373,7 +393,7 @@ class Context:
         return eta, min(m, max(1, m_max // b))
 
     def svrg_solve(self, B: np.ndarray, W0: np.ndarray, lam: float, mu: float,
-                   lam1_up: float, Y0: np.ndarray | None = None):
+                   lam1_up: float, Y0: np.ndarray | None = None, acc: AccStep | None = None):
         """Approximate (lambda I - X X^T)^{-1} B by SVRG epochs (Thm. 3).
 
         Epoch e: Wt = W; M = lambda Wt - X X^T Wt - B; stop when
@@ -381,6 +401,11 @@ class Context:
         inner steps on the stream (seed, SVRG, solve, e).  Stalls (an epoch that
         shrinks the residual by less than 10% after the third) end the solve at
         its floor; growth by more than 10x over the best residual is divergence.
+
+        With `acc` (one subproblem of acc_svrg_solve) the solve first checks the
+        original system's residual at the epoch-0 anchor and returns at once
+        (outer_done) when it is below tau ||B_orig||; its own stop is then
+        ||M|| <= max(tau ||B_orig||, acc_theta sqrt(q) ||r||).
         """
         o = self.opts
         eta, m = self.step_params(lam, mu, lam1_up)
@@ -403,8 +428,16 @@ class Context:
             if not np.isfinite(res) or res > 10.0 * best:
                 st.status = "diverged"
                 return W, st
+            tol = o.tau
+            if acc is not None:
+                if e == 0:
+                    st.outer_res = float(np.linalg.norm(M - acc.gamma * (Wt - acc.Z)))
+                    if o.fixed_epochs <= 0 and st.outer_res <= o.tau * acc.nB:
+                        st.outer_done = True
+                        return W, st
+                tol = max(o.tau * acc.nB, o.acc_theta * acc.sq * st.outer_res) / nB if nB > 0 else 0.0
             if o.fixed_epochs <= 0:
-                if res <= o.tau:
+                if res <= tol:
                     return W, st
                 if e >= 3 and res > 0.9 * prev:
                     return W, st
@@ -420,6 +453,83 @@ class Context:
             W = svrg_epoch(self.Xt, Wt, Wt, M, idx, self.table.c, eta, lam, b)
             st.inner_steps += m
             self.inner_steps += m
+        return W, st
+
+    def acc_gamma(self, lam: float, mu: float, lam1_up: float) -> float:
+        """Proximal weight gamma of the accelerated solve: 0 when an SVRG epoch
+        already draws at most `acc_target` samples (n by default), else the
+        gamma at which it draws exactly that many.  With lambda' = lambda + gamma,
+        mu' = mu + gamma, K = kappa lambda1_up / b and c = theta_m / theta_eta,
+        the uncapped epoch length is m b = b c (lambda'^2 + K) / mu'^2; setting it
+        to the target T gives (1 - a) g^2 + 2 (lambda - a mu) g + lambda^2 + K
+        - a mu^2 = 0 with a = T / (b c), whose positive root is taken."""
+        o = self.opts
+        b = max(1, int(o.batch))
+        T = float(o.acc_target if o.acc_target > 0 else self.n)
+        K = self.table.kappa * lam1_up / b
+        a = T * o.theta_eta / (b * o.theta_m)
+        C = lam * lam + K - a * mu * mu
+        if C <= 0.0 or a <= 1.0:
+            return 0.0
+        h = lam - a * mu
+        return (h + math.sqrt(h * h + (a - 1.0) * C)) / (a - 1.0)
+
+    def solve_linear(self, B: np.ndarray, W0: np.ndarray, lam: float, mu: float,
+                     lam1_up: float):
+        """(lambda I - A)^{-1} B by SVRG, accelerated when opts.acc is set."""
+        if self.opts.acc:
+            return self.acc_svrg_solve(B, W0, lam, mu, lam1_up)
+        return self.svrg_solve(B, W0, lam, mu, lam1_up)
+
+    def acc_svrg_solve(self, B: np.ndarray, W0: np.ndarray, lam: float, mu: float,
+                       lam1_up: float, inner=None):
+        """AccSVRGsolve (Sec. 1, Sec. 3, Cor. mainCond): the paper takes the
+        acceleration of Frostig et al. 2015 and does not print it.  Reading: an
+        accelerated proximal-point loop on F(W) = 1/2 tr W^T (lambda I - A) W
+        - tr B^T W, strongly convex with modulus mu.  Iteration s solves the
+        subproblem F(W) + gamma/2 ||W - Z_s||^2, i.e. the shifted system
+        ((lambda + gamma) I - A) W = B + gamma Z_s, by SVRG warm-started at W_s,
+        then extrapolates Z_{s+1} = W_{s+1} + beta (W_{s+1} - W_s) with
+        beta = (1 - sqrt q)/(1 + sqrt q), q = mu/(mu + gamma) (Nesterov's
+        constant momentum for a strongly convex objective).  gamma balances an
+        epoch at about n samples (acc_gamma); gamma = 0 is plain svrg_solve.
+        The loop ends when ||(lambda I - A) W_s - B|| <= tau ||B||, read off the
+        subproblem's first anchor.  `inner(R, W, lam', mu')`, if given, replaces
+        the SVRG subproblem solve (tests use an exact solve)."""
+        o = self.opts
+        gamma = self.acc_gamma(lam, mu, lam1_up)
+        if gamma <= 0.0 and inner is None:
+            return self.svrg_solve(B, W0, lam, mu, lam1_up)
+        q = mu / (mu + gamma)
+        sq = math.sqrt(q)
+        beta = (1.0 - sq) / (1.0 + sq)
+        nB = float(np.linalg.norm(B))
+        W = np.array(W0, dtype=np.float64, copy=True)
+        Z = W.copy()
+        st = SolveStats(status="notconv" if o.fixed_epochs <= 0 else "ok")
+        for s in range(o.acc_max_outer):
+            R = B + gamma * Z
+            if inner is not None:
+                Wn = inner(R, W, lam + gamma, mu + gamma)
+                sub = SolveStats(outer_res=float(np.linalg.norm(anchor(self.Xt, W, B, lam))))
+                sub.outer_done = o.fixed_epochs <= 0 and sub.outer_res <= o.tau * nB
+            else:
+                Wn, sub = self.svrg_solve(R, W, lam + gamma, mu + gamma, lam1_up,
+                                          acc=AccStep(gamma=gamma, Z=Z, nB=nB, sq=sq))
+            st.epochs += sub.epochs
+            st.inner_steps += sub.inner_steps
+            st.outer = s + 1
+            st.outer_res = sub.outer_res
+            st.residual = sub.outer_res / nB if nB > 0 else 0.0
+            if sub.status == "diverged":
+                st.status = "diverged"
+                return W, st
+            if sub.outer_done:
+                st.status = "ok"
+                st.outer_done = True
+                return W, st
+            Z = Wn + beta * (Wn - W)
+            W = Wn
         return W, st
 
 
@@ -501,13 +611,13 @@ def d_top_eig_inverse(ctx: Context, lam: float, mu: float, lam1_up: float, rnd: 
     scale = 1.0 / lam
     status = "ok"
     for _ in range(L):
-        w, st = ctx.svrg_solve(z, scale * z, lam, mu, lam1_up)
+        w, st = ctx.solve_linear(z, scale * z, lam, mu, lam1_up)
         if st.status == "diverged":
             return float("nan"), "diverged"
         nw = float(np.linalg.norm(w))
         scale = nw
         z = w / nw
-    w, st = ctx.svrg_solve(z, scale * z, lam, mu, lam1_up)
+    w, st = ctx.solve_linear(z, scale * z, lam, mu, lam1_up)
     if st.status == "diverged":
         return float("nan"), "diverged"
     lt = float(z[:, 0] @ w[:, 0])
@@ -678,7 +788,7 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
             W0 = S @ P
         else:
             W0 = np.zeros_like(S)
-        W, st = ctx.svrg_solve(S, W0, lam, mu, lam1_up)
+        W, st = ctx.solve_linear(S, W0, lam, mu, lam1_up)
         if st.status == "diverged":
             status = "diverged"
             break
