@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-outer", type=int, default=4)
     ap.add_argument("--max-outer", type=int, default=0, help="cap on outer iterations (0 = library default)")
     ap.add_argument("--batch", type=int, default=1, help="samples per SVRG inner step (power of two <= 16)")
+    ap.add_argument("--acc", action="store_true", help="accelerated SVRG solves (proximal-point loop)")
+    ap.add_argument("--acc-target", type=int, default=0, help="samples per epoch of an accelerated subproblem (0 = n)")
     ap.add_argument("--serve", action="store_true", help="request-loop benchmark instead")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mean-ms", type=float, default=20.0)
@@ -190,7 +192,8 @@ def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
     lh = O.lambda1_estimate(ctx)
     t_fixed = time.perf_counter() - t0
     o = O.Options(shift_policy=pol, delta=delta, min_outer=outer_sample, max_outer=outer_sample,
-                  tau=1e-3 if args.storage == "bf16" else 1e-5, batch=args.batch)
+                  tau=1e-3 if args.storage == "bf16" else 1e-5, batch=args.batch,
+                  acc=int(args.acc), acc_target=args.acc_target)
     t0 = time.perf_counter()
     r = O.solve(X64, wl.k, wl.p, args.eps, args.seed, o, lam1_hat=lh)
     t_outer = time.perf_counter() - t0
@@ -401,7 +404,8 @@ def run_lra(args):
     opt_val, lk, lp1 = spectrum(wl)
     delta = (lk - lp1) / 1.5
     pol = lra.LRA_SHIFT_FAR if args.shift == "far" else lra.LRA_SHIFT_PAPER
-    opt = lra.options(shift_policy=pol, delta=delta, profile=1, batch=args.batch)
+    opt = lra.options(shift_policy=pol, delta=delta, profile=1, batch=args.batch, acc=int(args.acc),
+                      acc_target=args.acc_target)
     if args.max_outer > 0:
         opt.max_outer = args.max_outer
 
@@ -544,6 +548,7 @@ def run_lra(args):
             "dtype": "f32" if storage_name == "csr" else args.storage, "data": "synthetic",
             "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
                        "storage": storage_name, "shift": args.shift, "eps": args.eps, "batch": args.batch,
+                       "acc": bool(args.acc),
                        "l2": "inputs larger than L2 (X %.2f GB per pass)" % (src.x_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"ratio_err_over_opt": ratio, "outer_iters": last.outer_iters,

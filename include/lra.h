@@ -98,6 +98,21 @@ typedef struct lra_options {
                                size becomes theta_eta mu/(lambda^2 + kappa lambda1_up / b) and
                                an epoch m = ceil(theta_m/(eta mu)) steps of b samples (at most
                                m_max samples).  Must be a power of two. */
+    int acc;                /* 1: accelerated solves (AccSVRGsolve, Sec. 1 and Cor. mainCond;
+                               the paper takes the acceleration of Frostig et al. 2015 without
+                               printing it).  Read as accelerated proximal point around SVRG:
+                               subproblem s solves ((lambda + gamma) I - X X^T) W = B + gamma Z_s
+                               by SVRG from W_s, then Z_{s+1} = W_{s+1} + beta (W_{s+1} - W_s),
+                               beta = (1 - sqrt q)/(1 + sqrt q), q = mu/(mu + gamma).  gamma is
+                               the smallest >= 0 at which an epoch draws at most acc_target
+                               samples (0 when plain SVRG already does: the plain solve runs).
+                               A subproblem stops at ||M|| <= max(tau ||B||, acc_theta sqrt(q)
+                               ||r_s||), r_s the original residual at W_s, read off its first
+                               anchor; the solve ends when ||r_s|| <= tau ||B||.  Default 0. */
+    double acc_theta;       /* subproblem accuracy factor in (0, 1]; default 0.5 */
+    int acc_max_outer;      /* subproblems per accelerated solve; default 200 (then LRA_ENOTCONV
+                               in lra_solve_info.status, the iterate is kept) */
+    int64_t acc_target;     /* samples per epoch the proximal weight aims for; 0 = n */
 } lra_options;
 
 typedef struct lra_report {
@@ -304,8 +319,13 @@ typedef struct lra_solve_info {
     int64_t inner_steps;
     int64_t m;             /* epoch length used */
     double eta;            /* step size used */
-    double residual;       /* ||M||_F / ||B||_F at the last anchor */
+    double residual;       /* ||M||_F / ||B||_F at the last anchor (accelerated: the original
+                              system's ||(lambda I - A) W - B||_F / ||B||_F at the last
+                              subproblem's first anchor) */
     int status;            /* LRA_OK, LRA_ENOTCONV (cap), LRA_EDIVERGED */
+    int outer;             /* accelerated solve: subproblems solved (solve ids solve_id ..
+                              solve_id + outer - 1); 0 for the plain solve */
+    double gamma;          /* accelerated solve: proximal weight (0 = plain solve ran) */
 } lra_solve_info;
 
 /* SVRGsolve (Sec. 2.3): W (device d x p, in: W0, out: solution) approximately
@@ -313,7 +333,8 @@ typedef struct lra_solve_info {
  * lambda1_up), m = ceil(theta_m / (eta mu)), epochs keyed (seed, SVRG,
  * solve_id, epoch).  Stops at ||M|| <= tau ||B|| (tau from opt), on a stall
  * (after the 4th anchor, a residual above 0.9 x the previous one), or at the
- * epoch cap. */
+ * epoch cap.  With opt->acc = 1 it is the accelerated solve (see
+ * lra_options.acc), subproblem s keyed as solve solve_id + s. */
 lra_status lra_svrg_solve(lra_mat *mat, int p, const float *B, float *W, double lambda, double mu,
                           double lambda1_up, uint64_t seed, int64_t solve_id,
                           const lra_options *opt, lra_solve_info *info);

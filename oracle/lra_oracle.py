@@ -462,7 +462,9 @@ class Context:
         mu' = mu + gamma, K = kappa lambda1_up / b and c = theta_m / theta_eta,
         the uncapped epoch length is m b = b c (lambda'^2 + K) / mu'^2; setting it
         to the target T gives (1 - a) g^2 + 2 (lambda - a mu) g + lambda^2 + K
-        - a mu^2 = 0 with a = T / (b c), whose positive root is taken."""
+        - a mu^2 = 0 with a = T / (b c), whose positive root is taken, raised by
+        1e-9 relative so that the epoch length ceil(...) is not decided by the
+        last bit of a value that sits exactly on the integer T / b."""
         o = self.opts
         b = max(1, int(o.batch))
         T = float(o.acc_target if o.acc_target > 0 else self.n)
@@ -472,7 +474,7 @@ class Context:
         if C <= 0.0 or a <= 1.0:
             return 0.0
         h = lam - a * mu
-        return (h + math.sqrt(h * h + (a - 1.0) * C)) / (a - 1.0)
+        return (h + math.sqrt(h * h + (a - 1.0) * C)) / (a - 1.0) * (1.0 + 1e-9)
 
     def solve_linear(self, B: np.ndarray, W0: np.ndarray, lam: float, mu: float,
                      lam1_up: float):

@@ -54,6 +54,10 @@ class LraOptions(C.Structure):
         ("trace_cap", C.c_int),
         ("profile", C.c_int),
         ("batch", C.c_int),
+        ("acc", C.c_int),
+        ("acc_theta", C.c_double),
+        ("acc_max_outer", C.c_int),
+        ("acc_target", C.c_int64),
     ]
 
 
@@ -109,6 +113,8 @@ class LraSolveInfo(C.Structure):
         ("eta", C.c_double),
         ("residual", C.c_double),
         ("status", C.c_int),
+        ("outer", C.c_int),
+        ("gamma", C.c_double),
     ]
 
 

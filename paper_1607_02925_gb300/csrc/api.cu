@@ -131,6 +131,10 @@ void lra_options_default(lra_options *opt) {
     opt->warm_start = 1;
     opt->max_shift_rounds = 30;
     opt->batch = 1;
+    opt->acc = 0;
+    opt->acc_theta = 0.5;
+    opt->acc_max_outer = 200;
+    opt->acc_target = 0;
 }
 
 const char *lra_status_str(lra_status s) {
@@ -678,7 +682,8 @@ lra_status lra_svrg_solve(lra_mat *mat, int p, const float *B, float *W, double 
         pb.upload(B, mat->d, mat->dpad, p);
         pw.upload(W, mat->d, mat->dpad, p);
         SolveInfo si;
-        const lra_status st = e.svrg_solve(pb.p, pw.p, p, lambda, mu, lambda1_up, seed, solve_id, o, nullptr, si);
+        int64_t sc = solve_id;
+        const lra_status st = e.solve_linear(pb.p, pw.p, p, lambda, mu, lambda1_up, seed, sc, o, nullptr, si);
         pw.download(W, mat->d, mat->dpad, p);
         LRA_CUDA(cudaStreamSynchronize(ctx->stream));
         if (info) {
@@ -688,6 +693,8 @@ lra_status lra_svrg_solve(lra_mat *mat, int p, const float *B, float *W, double 
             info->eta = si.eta;
             info->residual = si.residual;
             info->status = si.status;
+            info->outer = si.outer;
+            info->gamma = si.gamma;
         }
         return st;
     })

@@ -68,12 +68,17 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
         r.trace_cap = o->trace_cap;
         r.profile = o->profile;
         r.batch = o->batch;
+        r.acc = o->acc;
+        r.acc_theta = o->acc_theta;
+        r.acc_max_outer = o->acc_max_outer;
+        r.acc_target = o->acc_target;
     }
     if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
     if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
         r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
         r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0) || r.batch < 1 || r.batch > 16 ||
-        (r.batch & (r.batch - 1)) != 0) {
+        (r.batch & (r.batch - 1)) != 0 || r.acc < 0 || r.acc > 1 || !(r.acc_theta > 0.0 && r.acc_theta <= 1.0) ||
+        r.acc_max_outer < 1 || r.acc_target < 0) {
         set_error("invalid lra_options field");
         throw Error{LRA_EINVAL};
     }
@@ -87,7 +92,7 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
     const int PP = pad_p(pmax);
     const int nch = sp_items >= 0 ? 1 : std::max(xy_chunks(dpad, n, 128), xy_chunks(dpad, n, 256));
     size_t b = 0;
-    b += 6 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U
+    b += 9 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U, accelerated solve: Za Ra Wo
     b += sizeof(float) * dpad * PP;             // Wr
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
@@ -117,6 +122,9 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         M = alloc<float>(blk);
         T1 = alloc<float>(blk);
         U = alloc<float>(blk);
+        Za = alloc<float>(blk);
+        Ra = alloc<float>(blk);
+        Wo = alloc<float>(blk);
         Wr = alloc<float>((size_t)dpad * PPmax);
         Q = alloc<float>((size_t)n * PPmax);
         Y = alloc<float>((size_t)n * PPmax);
@@ -508,7 +516,7 @@ void Engine::step_params(double lam, double mu, double l1up, double kappa, const
 
 lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
                               uint64_t seed, int64_t solve_id, const Opts &o, const float *G0,
-                              SolveInfo &info) {
+                              SolveInfo &info, const AccHook *acc) {
     const auto &tab = ensure_table(o.sampling);
     double eta;
     int64_t m;
@@ -532,8 +540,26 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
             info.status = LRA_EDIVERGED;
             return LRA_EDIVERGED;
         }
+        double tol = o.tau;
+        if (acc) {
+            if (e == 0) {
+                // the original system's residual at W: M - gamma (W - Z)
+                acc_resid(s_, ws_.M, ws_.Wt, acc->Z, mat_->dpad, mat_->dpad, p, acc->gamma, ws_.dots);
+                LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.dots, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
+                sync();
+                double r2 = 0.0;
+                for (int j = 0; j < p; ++j) r2 += ws_.host[j];
+                info.outer_res = std::sqrt(r2);
+                if (o.fixed_epochs <= 0 && info.outer_res <= o.tau * acc->nB) {
+                    info.outer_done = true;
+                    return LRA_OK;
+                }
+            }
+            tol = nB2 > 0 ? std::max(o.tau * acc->nB, o.acc_theta * acc->sq * info.outer_res) / std::sqrt(nB2)
+                          : 0.0;
+        }
         if (o.fixed_epochs <= 0) {
-            if (res <= o.tau) return LRA_OK;
+            if (res <= tol) return LRA_OK;
             if (e >= 3 && res > 0.9 * prev) return LRA_OK;
         }
         if (e == max_e - 1) {
@@ -551,6 +577,82 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
         stats.inner_steps += m;
     }
     return LRA_OK;
+}
+
+double Engine::acc_gamma(double lam, double mu, double l1up, double kappa, const Opts &o) const {
+    // Smallest gamma >= 0 at which an SVRG epoch of the subproblem
+    // ((lam + g) I - A) draws at most T samples: with K = kappa l1up / b and
+    // c = theta_m / theta_eta the uncapped epoch is b c ((lam + g)^2 + K) /
+    // (mu + g)^2 samples; equal to T at the positive root of
+    // (1 - a) g^2 + 2 (lam - a mu) g + lam^2 + K - a mu^2 = 0, a = T / (b c),
+    // raised by 1e-9 relative so that ceil() of the epoch length is not decided
+    // by the last bit of a value sitting exactly on the integer T / b.
+    const int b = std::max(1, o.batch);
+    const double T = (double)(o.acc_target > 0 ? o.acc_target : mat_->n);
+    const double K = kappa * l1up / b;
+    const double a = T * o.theta_eta / (b * o.theta_m);
+    const double C = lam * lam + K - a * mu * mu;
+    if (C <= 0.0 || a <= 1.0) return 0.0;
+    const double h = lam - a * mu;
+    return (h + std::sqrt(h * h + (a - 1.0) * C)) / (a - 1.0) * (1.0 + 1e-9);
+}
+
+lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
+                             uint64_t seed, int64_t &solve_count, const Opts &o, const float *G0,
+                             SolveInfo &info) {
+    // AccSVRGsolve (Sec. 1, Cor. mainCond; the acceleration of Frostig et al.,
+    // which the paper does not print): accelerated proximal point on
+    // F(W) = 1/2 tr W^T (lam I - A) W - tr B^T W.  Subproblem s is the
+    // shifted system ((lam + gamma) I - A) W = B + gamma Z_s, solved by SVRG
+    // from W_s; then Z_{s+1} = W_{s+1} + beta (W_{s+1} - W_s) with
+    // beta = (1 - sqrt q) / (1 + sqrt q), q = mu / (mu + gamma).  The loop ends
+    // when the original residual, read off a subproblem's first anchor, is
+    // below tau ||B||; no X pass is added.
+    const auto &tab = ensure_table(o.sampling);
+    const double gamma = acc_gamma(lam, mu, l1up, tab.kappa, o);
+    if (!(gamma > 0.0)) return svrg_solve(B, W, p, lam, mu, l1up, seed, solve_count++, o, G0, info);
+    const double q = mu / (mu + gamma), sq = std::sqrt(q), beta = (1.0 - sq) / (1.0 + sq);
+    const int64_t dpad = mat_->dpad;
+    col_dots(s_, B, B, dpad, dpad, p, ws_.dots);
+    acc_extrapolate(s_, W, ws_.Wo, ws_.Za, ws_.Ra, B, dpad, dpad, p, 0.0f, (float)gamma, true);
+    LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.dots, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
+    sync();
+    double b2 = 0.0;
+    for (int j = 0; j < p; ++j) b2 += ws_.host[j];
+    const AccHook hook{gamma, std::sqrt(b2), sq, ws_.Za};
+    info = SolveInfo();
+    info.gamma = gamma;
+    info.status = o.fixed_epochs > 0 ? LRA_OK : LRA_ENOTCONV;
+    for (int s = 0; s < o.acc_max_outer; ++s) {
+        SolveInfo sub;
+        const lra_status st = svrg_solve(ws_.Ra, W, p, lam + gamma, mu + gamma, l1up, seed, solve_count++, o,
+                                         s == 0 ? G0 : nullptr, sub, &hook);
+        info.epochs += sub.epochs;
+        info.inner_steps += sub.inner_steps;
+        info.m = sub.m;
+        info.eta = sub.eta;
+        info.outer = s + 1;
+        info.outer_res = sub.outer_res;
+        info.residual = hook.nB > 0 ? sub.outer_res / hook.nB : 0.0;
+        if (st != LRA_OK || sub.status == LRA_EDIVERGED) {
+            info.status = LRA_EDIVERGED;
+            return LRA_EDIVERGED;
+        }
+        if (sub.outer_done) {
+            info.status = LRA_OK;
+            info.outer_done = true;
+            return LRA_OK;
+        }
+        acc_extrapolate(s_, W, ws_.Wo, ws_.Za, ws_.Ra, B, dpad, dpad, p, (float)beta, (float)gamma, false);
+    }
+    return LRA_OK;
+}
+
+lra_status Engine::solve_linear(const float *B, float *W, int p, double lam, double mu, double l1up,
+                                uint64_t seed, int64_t &solve_count, const Opts &o, const float *G0,
+                                SolveInfo &info) {
+    if (o.acc) return acc_solve(B, W, p, lam, mu, l1up, seed, solve_count, o, G0, info);
+    return svrg_solve(B, W, p, lam, mu, l1up, seed, solve_count++, o, G0, info);
 }
 
 double Engine::lambda1_estimate(uint64_t seed) {
@@ -584,7 +686,7 @@ lra_status Engine::d_top_inverse(uint64_t seed, int rnd, double lam, double mu, 
     for (int l = 0; l <= L; ++l) {
         LRA_CUDA(cudaMemcpyAsync(w, z, sizeof(float) * dpad, cudaMemcpyDeviceToDevice, s_));
         scale_block(s_, w, dpad, dpad, 1, (float)scale);
-        const lra_status st = svrg_solve(z, w, 1, lam, mu, l1up, seed, solve_count++, o, nullptr, info);
+        const lra_status st = solve_linear(z, w, 1, lam, mu, l1up, seed, solve_count, o, nullptr, info);
         if (st != LRA_OK || info.status == LRA_EDIVERGED) return LRA_EDIVERGED;
         if (l == L) {
             const double lt = dot1(z, w);
@@ -787,7 +889,7 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
             LRA_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * dpad * p, s_));
         }
         SolveInfo info;
-        st = svrg_solve(S, W, p, lam, mu, l1up, seed, solve_count++, o, G0, info);
+        st = solve_linear(S, W, p, lam, mu, l1up, seed, solve_count, o, G0, info);
         if (st != LRA_OK) return st;
         R.eta = info.eta;
         R.m = info.m;

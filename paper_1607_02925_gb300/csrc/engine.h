@@ -81,6 +81,10 @@ struct Opts {
     int trace_cap = 0;
     int profile = 0;
     int batch = 1;
+    int acc = 0;               // accelerated solves (proximal-point loop around SVRG)
+    double acc_theta = 0.5;
+    int acc_max_outer = 200;
+    int64_t acc_target = 0;    // samples per epoch the proximal weight aims for; 0 = n
 };
 
 // CUDA-event timing of individual kernel launches on the engine's stream.
@@ -114,6 +118,19 @@ struct SolveInfo {
     double eta = 0.0;
     double residual = NAN;
     lra_status status = LRA_OK;
+    // accelerated solves: subproblems solved, proximal weight, and the residual
+    // ||(lambda I - A) W - B||_F read at the last subproblem's first anchor
+    int outer = 0;
+    double gamma = 0.0;
+    double outer_res = NAN;
+    bool outer_done = false;
+};
+
+// One subproblem of an accelerated solve: the system solved is
+// ((lambda + gamma) I - A) W = B + gamma Z; nB = ||B||_F of the original system.
+struct AccHook {
+    double gamma, nB, sq;
+    const float *Z;
 };
 
 struct Stats {
@@ -135,6 +152,7 @@ struct Workspace {
     double *H = nullptr, *Hc = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;
+    float *Za = nullptr, *Ra = nullptr, *Wo = nullptr;  // accelerated solve: Z, B + gamma Z, previous W
     __nv_bfloat16 *Wb = nullptr, *Yb = nullptr;  // BF16 hi/lo operands of the tensor-core passes
     int64_t ldy = 0;
     int *status = nullptr;
@@ -205,7 +223,17 @@ class Engine {
                      int64_t &m) const;
     lra_status svrg_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
                           uint64_t seed, int64_t solve_id, const Opts &o, const float *G0,
-                          SolveInfo &info);
+                          SolveInfo &info, const AccHook *acc = nullptr);
+    // proximal weight of the accelerated solve (0: plain SVRG already balanced)
+    double acc_gamma(double lam, double mu, double l1up, double kappa, const Opts &o) const;
+    // accelerated solve; one solve id per subproblem (solve_count advances by info.outer)
+    lra_status acc_solve(const float *B, float *W, int p, double lam, double mu, double l1up,
+                         uint64_t seed, int64_t &solve_count, const Opts &o, const float *G0,
+                         SolveInfo &info);
+    // (lambda I - A)^{-1} B: acc_solve when o.acc is set, else svrg_solve
+    lra_status solve_linear(const float *B, float *W, int p, double lam, double mu, double l1up,
+                            uint64_t seed, int64_t &solve_count, const Opts &o, const float *G0,
+                            SolveInfo &info);
     double lambda1_estimate(uint64_t seed);
     lra_status d_top_inverse(uint64_t seed, int rnd, double lam, double mu, double l1up,
                              const Opts &o, int64_t &solve_count, double &inv);

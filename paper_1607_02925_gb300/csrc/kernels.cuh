@@ -130,6 +130,12 @@ void col_dots(cudaStream_t s, const float *A, const float *B, int64_t rows, int6
 void scale_cols_rsqrt(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, const double *n2);
 // A = alpha * A (all rows x p)
 void scale_block(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, float alpha);
+// out[j] = sum_r (M - gamma (Wt - Z))[r, j]^2 (FP64), one block per column
+void acc_resid(cudaStream_t s, const float *M, const float *Wt, const float *Z, int64_t rows, int64_t ld,
+               int p, double gamma, double *out);
+// Z = W + beta (W - Wold), Wold = W, R = B + gamma Z; first: Z = W (Wold not read)
+void acc_extrapolate(cudaStream_t s, const float *W, float *Wold, float *Z, float *R, const float *B,
+                     int64_t rows, int64_t ld, int p, float beta, float gamma, bool first);
 
 // ---- sparse X (k_sparse.cu) -----------------------------------------------
 // Segment length of the row work list of X Y (rows longer than this are split).

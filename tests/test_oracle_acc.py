@@ -52,7 +52,11 @@ def test_gamma_balances_the_epoch(batch, target):
         mu = lam - lam1
         g = ctx.acc_gamma(lam, mu, lam1)
         assert g > 0.0
-        assert _epoch_samples(ctx, lam + g, mu + g, lam1) == pytest.approx(T, rel=1e-9)
+        # at the target (from below, by the 1e-9 relative nudge of gamma)
+        e = _epoch_samples(ctx, lam + g, mu + g, lam1)
+        assert e == pytest.approx(T, rel=1e-8) and e < T
+        step = ctx.step_params(lam + g, mu + g, lam1)[1]
+        assert step == math.ceil(T / batch)
         # the smallest such gamma: a little less is over the target
         assert _epoch_samples(ctx, lam + 0.99 * g, mu + 0.99 * g, lam1) > T
     # an epoch already within the target: no proximal term
