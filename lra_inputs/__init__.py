@@ -77,6 +77,21 @@ def sigma_exp_two_gaps(r: int = 640) -> np.ndarray:
     return s
 
 
+def sigma_partition(r: int = 64) -> np.ndarray:
+    """Spectrum for Algorithm 6's branches with k = 3, p = 4 (lambda = sigma^2):
+    lambda_1 = 40 (a multiplicative gap to lambda_2 = 10), lambda_2..4 = 10, 9.6,
+    9.3 (relative steps 4% and 3%, below p^-2 = 6.25%), lambda_5 = 8.85
+    (lambda_3 - lambda_5 = 0.75 = 1.5 Delta with Delta = 0.5, so the 0.4 gap after
+    lambda_2 exceeds 5 Delta / 9 and the 0.3 one after lambda_3 does not), then
+    lambda_i = 2 (i / 6)^-1 for i >= 6."""
+    lam = np.zeros(r)
+    head = [40.0, 10.0, 9.6, 9.3, 8.85]
+    lam[: len(head)] = head
+    i = np.arange(len(head) + 1, r + 1, dtype=np.float64)
+    lam[len(head):] = 2.0 * (i / 6.0) ** -1
+    return np.sqrt(lam)
+
+
 def sigma_serving(k: int, r: int) -> np.ndarray:
     """Small-gap spectrum rescaled to rank k (p = 2k): k=5 gives sigma_small_gap.
 
@@ -266,6 +281,8 @@ class Workload:
             return sigma_steep_head(self.r)
         if self.name.startswith("exp_two_gaps"):
             return sigma_exp_two_gaps(self.r)
+        if self.name.startswith("partition"):
+            return sigma_partition(self.r)
         raise ValueError(f"{self.name} has no planted spectrum")
 
     def csr(self):
@@ -287,6 +304,9 @@ WORKLOADS = {
     "exp_two_gaps_8192x1048576": Workload("exp_two_gaps_8192x1048576", 8192, 1048576, 50, 100, 640, 3, "bf16"),
     # the same spectrum and d with n = 65536 (X = 1.07 GB BF16): profiling captures
     "exp_two_gaps_8192x65536": Workload("exp_two_gaps_8192x65536", 8192, 65536, 50, 100, 640, 3, "bf16"),
+    # Algorithm 6's branches (a multiplicative gap, then an additive one): FP64,
+    # d=64, n=800, k=3, p=4, Delta = 0.5
+    "partition_64x800": Workload("partition_64x800", 64, 800, 3, 4, 64, 5, "f64"),
     # sparse CSR (Zipf term-document), d=50000, n=500000, ~100 non-zeros per column
     "zipf_csr_50000x500000": Workload("zipf_csr_50000x500000", 50000, 500000, 10, 20, 0, 4, "csr"),
     # the same law at d=2000, n=20000 (tests and the reference optimum's cross-check)

@@ -772,15 +772,47 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
         if not mu > 0:
             raise ValueError("fixed shift must exceed lambda_1 / (1 - 1/4)")
 
+    sub = subspace_on_d(ctx, k, p, eps, seed, lam, mu, lam1_up)
+    S, rho, Uh = sub.S, sub.rho, sub.Uh
+    if Xt_final is not None:
+        rho, Uh, Q, H = rayleigh_ritz(Xt_final, S)
+        ctx.x_passes += 1
+    U = S @ Uh[:, :k]
+    return Result(U=U, ritz=rho[:k].copy(), lam=lam, lam1_hat=lam1_hat, delta=delta,
+                  outer_iters=sub.outer_iters, E_trace=sub.E_trace, shift=shift, status=sub.status,
+                  solves=ctx.solve_count, epochs=ctx.epochs, inner_steps=ctx.inner_steps,
+                  x_passes=ctx.x_passes, S=S)
+
+
+@dataclass
+class SubspaceResult:
+    S: np.ndarray           # final orthonormal basis (d x p)
+    rho: np.ndarray         # its Ritz values with C = A, descending
+    Uh: np.ndarray          # Ritz vectors in the basis (p x p)
+    outer_iters: int
+    E_trace: list
+    status: str
+
+
+def subspace_on_d(ctx: Context, k: int, p: int, eps: float, seed: int, lam: float, mu: float,
+                  lam1_up: float, r_floor: float | None = None) -> SubspaceResult:
+    """Algorithm 1 on D = (lambda I - A)^{-1} (A of ctx's X) with p columns from
+    the Gaussian start (seed, INIT), Rayleigh-Ritz with C = A every iteration
+    (Algorithm 2), stopped by outer_stop on E_l = ||X||_F^2 - sum_{j<=k} rho_j
+    with the rate floor r_floor (default: theory_rate from rho_k and rho_p;
+    without oversampling, p = k, the caller supplies it)."""
+    opts = ctx.opts
+    d = ctx.d
     S = orth(gaussian_block(seed, STREAM_INIT, 0, d, p))
     E: list[float] = []
     status = "ok"
     ell = 0
     while True:
-        rho, Uh, Q, H = rayleigh_ritz(Xt, S)
+        rho, Uh, Q, H = rayleigh_ritz(ctx.Xt, S)
         ctx.x_passes += 1
         E.append(ctx.fro2 - float(np.sum(rho[:k])))
-        if outer_stop(E, eps, ell, opts.min_outer, theory_rate(lam, rho, k, p)):
+        rf = theory_rate(lam, rho, k, p) if r_floor is None else r_floor
+        if outer_stop(E, eps, ell, opts.min_outer, rf):
             break
         if ell >= opts.max_outer:
             status = "notconv"
@@ -796,14 +828,7 @@ def solve(Xt: np.ndarray, k: int, p: int, eps: float, seed: int, opts: Options |
             break
         S = orth(W)
         ell += 1
-    if Xt_final is not None:
-        rho, Uh, Q, H = rayleigh_ritz(Xt_final, S)
-        ctx.x_passes += 1
-    U = S @ Uh[:, :k]
-    return Result(U=U, ritz=rho[:k].copy(), lam=lam, lam1_hat=lam1_hat, delta=delta,
-                  outer_iters=ell, E_trace=E, shift=shift, status=status,
-                  solves=ctx.solve_count, epochs=ctx.epochs, inner_steps=ctx.inner_steps,
-                  x_passes=ctx.x_passes, S=S)
+    return SubspaceResult(S=S, rho=rho, Uh=Uh, outer_iters=ell, E_trace=E, status=status)
 
 
 # ----------------------------------------------------------------------------
