@@ -66,7 +66,10 @@ enum { LRA_SAMPLE_IMPORTANCE = 0, LRA_SAMPLE_UNIFORM = 1 };
 
 /* Counter-stream identifiers (the randomness of the method; see lra_stream_key). */
 enum { LRA_STREAM_INIT = 1, LRA_STREAM_POWER_A = 2, LRA_STREAM_POWER_D = 3,
-       LRA_STREAM_SVRG = 4, LRA_STREAM_DELTA = 5 };
+       LRA_STREAM_SVRG = 4, LRA_STREAM_DELTA = 5,
+       LRA_STREAM_PART = 6,    /* stage seeds of Algorithm 6: stream_key(seed, PART, t, 0) */
+       LRA_STREAM_BLOCK = 7 }; /* Gaussian starts of Algorithm 3 (a = 0 on A, 2 on D) and of
+                                  Algorithm 1 on A (a = 1) within a stage */
 
 /* Largest oversampling p supported (the p x p eigenproblem runs in one CTA). */
 #define LRA_MAX_P 112
@@ -113,6 +116,18 @@ typedef struct lra_options {
     int acc_max_outer;      /* subproblems per accelerated solve; default 200 (then LRA_ENOTCONV
                                in lra_solve_info.status, the iterate is kept) */
     int64_t acc_target;     /* samples per epoch the proximal weight aims for; 0 = n */
+    int partition;          /* 1: Algorithm 6 in full (Sec. 3): adaptive partitioning of {1..k}
+                               with deflation.  Stage t at index s forms X_{-(s-1)} =
+                               (I - U U^T) X explicitly (dense, the original storage; FP32 for
+                               a CSR X), runs Algorithm 3 on A_{-(s-1)} (eps' = 1/(9 p^2)) and
+                               Algorithm 4; a multiplicative gap gives Algorithm 1 on A with
+                               q - s + 1 columns, otherwise Algorithm 7, Algorithm 3 on
+                               D_{-(s-1)} (eps' = 1/(9p)), Algorithm 5 and Algorithm 1 on D
+                               with q - s + 1 columns (q < k) or p - (s - 1) (q = k).  Stage
+                               randomness is keyed by stream_key(seed, PART, t, 0).  Needs
+                               Delta (or p + 1 <= LRA_MAX_P to estimate it); shift_policy is
+                               not used.  Default 0 (the q = k branch at s = 1). */
+    int part_max_iters;     /* cap on Algorithm 3's ceil(eps'^-1 ln(d/eps')) iterations; default 2000 */
 } lra_options;
 
 typedef struct lra_report {
@@ -146,6 +161,12 @@ typedef struct lra_report {
      * matrices and their correction, [4] eigensolver, [5] CholeskyQR2,
      * [6] basis rotation and warm start, [7] anchor epilogue and sampling */
     double phase_ms[8];
+    /* options.partition = 1: stages of Algorithm 6, the last index q each found
+     * and how (1 = Algorithm 4's multiplicative gap and Algorithm 1 on A,
+     * 2 = shift-and-invert: Algorithms 7, 5 and 1 on D) */
+    int part_stages;
+    int part_q[LRA_MAX_P];
+    int part_kind[LRA_MAX_P];
 } lra_report;
 
 /* ---------------------------------------------------------------------------

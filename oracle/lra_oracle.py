@@ -400,7 +400,9 @@ class Context:
         ||M||_F <= tau ||B||_F (or after `fixed_epochs` anchors); otherwise m
         inner steps on the stream (seed, SVRG, solve, e).  Stalls (an epoch that
         shrinks the residual by less than 10% after the third) end the solve at
-        its floor; growth by more than 10x over the best residual is divergence.
+        its floor; a residual above both 10x the best and the first one is
+        divergence (a rebound at the rounding floor, far below the start, is a
+        stall).
 
         With `acc` (one subproblem of acc_svrg_solve) the solve first checks the
         original system's residual at the epoch-0 anchor and returns at once
@@ -416,6 +418,7 @@ class Context:
         st = SolveStats()
         best = float("inf")
         prev = float("inf")
+        res0 = float("inf")
         max_e = o.fixed_epochs if o.fixed_epochs > 0 else o.max_epochs
         for e in range(max_e):
             Wt = W
@@ -425,7 +428,9 @@ class Context:
             st.epochs = e + 1
             st.residual = res
             self.epochs += 1
-            if not np.isfinite(res) or res > 10.0 * best:
+            if e == 0:
+                res0 = res
+            if not np.isfinite(res) or (res > 10.0 * best and res > res0):
                 st.status = "diverged"
                 return W, st
             tol = o.tau
@@ -496,8 +501,11 @@ class Context:
         constant momentum for a strongly convex objective).  gamma balances an
         epoch at about n samples (acc_gamma); gamma = 0 is plain svrg_solve.
         The loop ends when ||(lambda I - A) W_s - B|| <= tau ||B||, read off the
-        subproblem's first anchor.  `inner(R, W, lam', mu')`, if given, replaces
-        the SVRG subproblem solve (tests use an exact solve)."""
+        subproblem's first anchor, or at a stall: after w = max(3, ceil(2/sqrt q))
+        subproblems (an expected contraction of e^-2), a residual above half the
+        one w subproblems before (the rounding floor of the path).
+        `inner(R, W, lam', mu')`, if given, replaces the SVRG subproblem solve
+        (tests use an exact solve)."""
         o = self.opts
         gamma = self.acc_gamma(lam, mu, lam1_up)
         if gamma <= 0.0 and inner is None:
@@ -509,6 +517,8 @@ class Context:
         W = np.array(W0, dtype=np.float64, copy=True)
         Z = W.copy()
         st = SolveStats(status="notconv" if o.fixed_epochs <= 0 else "ok")
+        w = max(3, int(math.ceil(2.0 / sq)))
+        hist: list[float] = []
         for s in range(o.acc_max_outer):
             R = B + gamma * Z
             if inner is not None:
@@ -529,6 +539,10 @@ class Context:
             if sub.outer_done:
                 st.status = "ok"
                 st.outer_done = True
+                return W, st
+            hist.append(sub.outer_res)
+            if o.fixed_epochs <= 0 and len(hist) > w and hist[-1] > 0.5 * hist[-1 - w]:
+                st.status = "ok"
                 return W, st
             Z = Wn + beta * (Wn - W)
             W = Wn

@@ -58,6 +58,8 @@ class LraOptions(C.Structure):
         ("acc_theta", C.c_double),
         ("acc_max_outer", C.c_int),
         ("acc_target", C.c_int64),
+        ("partition", C.c_int),
+        ("part_max_iters", C.c_int),
     ]
 
 
@@ -95,6 +97,9 @@ class LraReport(C.Structure):
         ("xtw_cols", C.c_int64),
         ("xy_cols", C.c_int64),
         ("phase_ms", C.c_double * 8),
+        ("part_stages", C.c_int),
+        ("part_q", C.c_int * LRA_MAX_P),
+        ("part_kind", C.c_int * LRA_MAX_P),
     ]
 
     def __init__(self):

@@ -135,6 +135,8 @@ void lra_options_default(lra_options *opt) {
     opt->acc_theta = 0.5;
     opt->acc_max_outer = 200;
     opt->acc_target = 0;
+    opt->partition = 0;
+    opt->part_max_iters = 2000;
 }
 
 const char *lra_status_str(lra_status s) {
@@ -464,6 +466,15 @@ lra_status lra_solve(lra_mat *mat, int k, int p, double eps, uint64_t seed, cons
             lra_mat *m;
             ~Release() { m->busy.fetch_sub(1); }
         } rel{mat};
+        if (o.partition) {
+            if (!(o.delta > 0) && p + 1 > LRA_MAX_P) {
+                set_error("estimating Delta needs p + 1 <= LRA_MAX_P");
+                return LRA_EUNSUPPORTED;
+            }
+            const lra_status st = solve_partitioned(mat, k, p, eps, seed, o, U, ritz, rep);
+            if (st != LRA_OK && st != LRA_ENOTCONV && rep) rep->status = st;
+            return st;
+        }
         Workspace ws(ctx, mat->dpad, mat->n, pmax, nullptr, ws_items(mat));
         Engine e(mat, ws, ctx->stream);
         const lra_status st = e.solve(k, p, eps, seed, o, U, ritz, rep, nullptr);

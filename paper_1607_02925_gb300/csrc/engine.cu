@@ -72,13 +72,15 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
         r.acc_theta = o->acc_theta;
         r.acc_max_outer = o->acc_max_outer;
         r.acc_target = o->acc_target;
+        r.partition = o->partition;
+        r.part_max_iters = o->part_max_iters;
     }
     if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
     if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
         r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
         r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0) || r.batch < 1 || r.batch > 16 ||
         (r.batch & (r.batch - 1)) != 0 || r.acc < 0 || r.acc > 1 || !(r.acc_theta > 0.0 && r.acc_theta <= 1.0) ||
-        r.acc_max_outer < 1 || r.acc_target < 0) {
+        r.acc_max_outer < 1 || r.acc_target < 0 || r.partition < 0 || r.partition > 1 || r.part_max_iters < 1) {
         set_error("invalid lra_options field");
         throw Error{LRA_EINVAL};
     }
@@ -527,7 +529,7 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
     stats.solves += 1;
     const size_t blk = sizeof(float) * mat_->dpad * p;
     const int max_e = o.fixed_epochs > 0 ? o.fixed_epochs : o.max_epochs;
-    double best = INFINITY, prev = INFINITY;
+    double best = INFINITY, prev = INFINITY, res0 = INFINITY;
     for (int e = 0; e < max_e; ++e) {
         LRA_CUDA(cudaMemcpyAsync(ws_.Wt, W, blk, cudaMemcpyDeviceToDevice, s_));
         double nM2, nB2;
@@ -536,7 +538,13 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
         const double res = nB2 > 0 ? std::sqrt(nM2 / nB2) : 0.0;
         info.epochs = e + 1;
         info.residual = res;
-        if (!std::isfinite(res) || res > 10.0 * best) {
+        if (e == 0) res0 = res;
+        // divergence: above 10x the best and above the start (a rebound at the
+        // rounding floor, far below the start, is left to the stall rule)
+        if (!std::isfinite(res) || (res > 10.0 * best && res > res0)) {
+            set_error("SVRG: residual " + std::to_string(res) + " after a best of " + std::to_string(best) +
+                      " at epoch " + std::to_string(e) + " (lambda " + std::to_string(lam) + ", mu " +
+                      std::to_string(mu) + ", p " + std::to_string(p) + ")");
             info.status = LRA_EDIVERGED;
             return LRA_EDIVERGED;
         }
@@ -623,6 +631,10 @@ lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double
     info = SolveInfo();
     info.gamma = gamma;
     info.status = o.fixed_epochs > 0 ? LRA_OK : LRA_ENOTCONV;
+    // stall: after w subproblems (an expected contraction of e^-2) a residual
+    // above half the one w before, the rounding floor of the path
+    const int w = std::max(3, (int)std::ceil(2.0 / sq));
+    std::vector<double> hist;
     for (int s = 0; s < o.acc_max_outer; ++s) {
         SolveInfo sub;
         const lra_status st = svrg_solve(ws_.Ra, W, p, lam + gamma, mu + gamma, l1up, seed, solve_count++, o,
@@ -641,6 +653,11 @@ lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double
         if (sub.outer_done) {
             info.status = LRA_OK;
             info.outer_done = true;
+            return LRA_OK;
+        }
+        hist.push_back(sub.outer_res);
+        if (o.fixed_epochs <= 0 && (int)hist.size() > w && hist.back() > 0.5 * hist[hist.size() - 1 - w]) {
+            info.status = LRA_OK;
             return LRA_OK;
         }
         acc_extrapolate(s_, W, ws_.Wo, ws_.Za, ws_.Ra, B, dpad, dpad, p, (float)beta, (float)gamma, false);
@@ -690,12 +707,18 @@ lra_status Engine::d_top_inverse(uint64_t seed, int rnd, double lam, double mu, 
         if (st != LRA_OK || info.status == LRA_EDIVERGED) return LRA_EDIVERGED;
         if (l == L) {
             const double lt = dot1(z, w);
-            if (!(lt > 0.0) || !std::isfinite(lt)) return LRA_EDIVERGED;
+            if (!(lt > 0.0) || !std::isfinite(lt)) {
+                set_error("Algorithm 3 on D: z^T D z = " + std::to_string(lt) + " at lambda " + std::to_string(lam));
+                return LRA_EDIVERGED;
+            }
             inv = 1.0 / lt;
             return LRA_OK;
         }
         const double nw = std::sqrt(dot1(w, w));
-        if (!(nw > 0.0) || !std::isfinite(nw)) return LRA_EDIVERGED;
+        if (!(nw > 0.0) || !std::isfinite(nw)) {
+            set_error("Algorithm 3 on D: ||D z|| = " + std::to_string(nw) + " at lambda " + std::to_string(lam));
+            return LRA_EDIVERGED;
+        }
         scale = nw;
         LRA_CUDA(cudaMemcpyAsync(z, w, sizeof(float) * dpad, cudaMemcpyDeviceToDevice, s_));
         normalize(z);
@@ -791,6 +814,218 @@ static bool outer_stop(const std::vector<double> &E, double eps, int ell, int mi
     return remaining <= 0.25 * eps * E[n - 1];
 }
 
+static int alg3_iters(double eps, int64_t d, int cap) {
+    const double L = std::ceil((1.0 / eps) * std::log((double)d / eps));
+    return (int)std::max(1.0, std::min(L, (double)cap));
+}
+
+lra_status Engine::alg3_a(int kk, double eps, int cap, uint64_t seed, double *vals, int &iters) {
+    // Algorithm 3 with C = A: Algorithm 1 with kk columns for L steps, then the
+    // Ritz values of the final basis (Algorithm 2 with C = A)
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    const int L = alg3_iters(eps, d, cap);
+    float *S = ws_.S, *W = ws_.W;
+    gaussian(s_, stream_key(seed, LRA_STREAM_BLOCK, 0, 0), d, dpad, kk, S);
+    lra_status st = cholqr2(S, kk);
+    if (st != LRA_OK) return st;
+    for (int l = 0; l < L; ++l) {
+        a_apply(S, kk, W);
+        std::swap(S, W);
+        cholqr2(S, kk, true);
+        if ((l & 63) == 63) {
+            sync();
+            if ((st = qr_status()) != LRA_OK) return st;
+        }
+    }
+    a_apply(S, kk, W);
+    cross_gram(s_, S, nullptr, nullptr, W, dpad, dpad, kk, ws_.H, ws_.gscr);
+    sym_eig(s_, ws_.H, kk, ws_.evals, ws_.evecs, ws_.eigwork);
+    LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.evals, sizeof(double) * kk, cudaMemcpyDeviceToHost, s_));
+    sync();
+    if ((st = qr_status()) != LRA_OK) return st;
+    if (tc(false)) check_tc();
+    for (int j = 0; j < kk; ++j) {
+        vals[j] = ws_.host[j];
+        if (!std::isfinite(vals[j])) {
+            set_error("Algorithm 3: non-finite Ritz value");
+            return LRA_ENUMERIC;
+        }
+    }
+    iters = L;
+    return LRA_OK;
+}
+
+lra_status Engine::alg3_d(int kk, double eps, int cap, uint64_t seed, double lam, double mu, double l1up,
+                          double l1hat, const Opts &o, int64_t &solve_count, double *vals, int &iters) {
+    // Algorithm 3 with C = D = (lam I - A)^{-1}: every product D S a solve.  The
+    // solve of step l starts from the previous step's Galerkin projection of D,
+    // W0 = S C H C^T with H = sym(S_prev^T D S_prev) and C = S^T S_prev (kk x kk,
+    // on the host); the first from S / (lam - lambda_hat).
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    const int L = alg3_iters(eps, d, cap);
+    float *S = ws_.S, *W = ws_.W, *Sp = ws_.T1;
+    gaussian(s_, stream_key(seed, LRA_STREAM_BLOCK, 2, 0), d, dpad, kk, S);
+    lra_status st = cholqr2(S, kk);
+    if (st != LRA_OK) return st;
+    std::vector<double> Hh((size_t)kk * kk), Ch((size_t)kk * kk), T((size_t)kk * kk);
+    std::vector<float> Tf((size_t)kk * kk);
+    double *h = ws_.host;
+    for (int l = 0; l <= L; ++l) {
+        if (l == 0) {
+            LRA_CUDA(cudaMemcpyAsync(W, S, sizeof(float) * dpad * kk, cudaMemcpyDeviceToDevice, s_));
+            scale_block(s_, W, dpad, dpad, kk, (float)(1.0 / (lam - l1hat)));
+        } else {
+            cross_full(s_, S, Sp, dpad, dpad, kk, ws_.Gm, ws_.gscr);
+            LRA_CUDA(cudaMemcpyAsync(Ch.data(), ws_.Gm, sizeof(double) * kk * kk, cudaMemcpyDeviceToHost, s_));
+            sync();
+            // T = C H C^T (all column-major), then row-major FP32 for apply_right
+            for (int a = 0; a < kk; ++a)
+                for (int b = 0; b < kk; ++b) {
+                    double acc = 0.0;
+                    for (int i = 0; i < kk; ++i)
+                        for (int j = 0; j < kk; ++j)
+                            acc += Ch[a + (size_t)i * kk] * Hh[i + (size_t)j * kk] * Ch[b + (size_t)j * kk];
+                    T[a + (size_t)b * kk] = acc;
+                }
+            for (int a = 0; a < kk; ++a)
+                for (int b = 0; b < kk; ++b) Tf[(size_t)a * kk + b] = (float)T[a + (size_t)b * kk];
+            LRA_CUDA(cudaMemcpyAsync(ws_.P, Tf.data(), sizeof(float) * kk * kk, cudaMemcpyHostToDevice, s_));
+            apply_right(s_, S, dpad, 1, dpad, kk, ws_.P, kk, W, 1, dpad);
+        }
+        SolveInfo info;
+        st = solve_linear(S, W, kk, lam, mu, l1up, seed, solve_count, o, nullptr, info);
+        if (st != LRA_OK || info.status == LRA_EDIVERGED) return LRA_EDIVERGED;
+        cross_gram(s_, S, nullptr, nullptr, W, dpad, dpad, kk, ws_.H, ws_.gscr);
+        if (l == L) {
+            sym_eig(s_, ws_.H, kk, ws_.evals, ws_.evecs, ws_.eigwork);
+            LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * kk, cudaMemcpyDeviceToHost, s_));
+            sync();
+            if ((st = qr_status()) != LRA_OK) return st;
+            for (int j = 0; j < kk; ++j) {
+                vals[j] = h[j];
+                if (!(vals[j] > 0.0) || !std::isfinite(vals[j])) {
+                    set_error("Algorithm 3 on D: non-positive Ritz value");
+                    return LRA_EDIVERGED;
+                }
+            }
+            break;
+        }
+        LRA_CUDA(cudaMemcpyAsync(Hh.data(), ws_.H, sizeof(double) * kk * kk, cudaMemcpyDeviceToHost, s_));
+        LRA_CUDA(cudaMemcpyAsync(Sp, S, sizeof(float) * dpad * kk, cudaMemcpyDeviceToDevice, s_));
+        sync();
+        if (l > 0 && (st = qr_status()) != LRA_OK) return st;
+        std::swap(S, W);
+        st = cholqr2(S, kk, true);
+    }
+    if (tc(false)) check_tc();
+    iters = L;
+    return LRA_OK;
+}
+
+lra_status Engine::power_block(int b, double eps, double r_floor, uint64_t seed, const Opts &o, int &iters,
+                               lra_status &status) {
+    // Algorithm 1 on A with b columns and no oversampling (a block found by
+    // Algorithm 4); Rayleigh-Ritz with A each iteration and the outer loop's
+    // stop rule on E = ||X||_F^2 - sum of the b Ritz values
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    float *S = ws_.S, *W = ws_.W;
+    gaussian(s_, stream_key(seed, LRA_STREAM_BLOCK, 1, 0), d, dpad, b, S);
+    lra_status st = cholqr2(S, b);
+    if (st != LRA_OK) return st;
+    std::vector<double> E;
+    int ell = 0;
+    status = LRA_OK;
+    double *h = ws_.host;
+    while (true) {
+        ritz(S, b, false, 2, false);
+        LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * b, cudaMemcpyDeviceToHost, s_));
+        sync();
+        if (ell > 0 && (st = qr_status()) != LRA_OK) return st;
+        double sb = 0.0;
+        for (int j = 0; j < b; ++j) sb += h[j];
+        E.push_back(mat_->fro2 - sb);
+        if (outer_stop(E, eps, ell, o.min_outer, r_floor)) break;
+        if (ell >= o.max_outer) {
+            status = LRA_ENOTCONV;
+            break;
+        }
+        a_apply(S, b, W);
+        std::swap(S, W);
+        cholqr2(S, b, true);
+        ++ell;
+    }
+    // Ritz vectors S V into ws.U
+    evecs_to_rm(s_, ws_.evecs, b, b, ws_.P);
+    apply_right(s_, S, dpad, 1, dpad, b, ws_.P, b, ws_.U, 1, dpad);
+    if (tc(false)) check_tc();
+    iters = ell;
+    return LRA_OK;
+}
+
+lra_status Engine::loop_d(int k, int p, double eps, uint64_t seed, double lam, double mu, double l1up,
+                          const Opts &o, int64_t &solve_count, double r_floor, float *&S_out, int &ell,
+                          std::vector<double> &E, lra_status &status, lra_report &R,
+                          const std::atomic<int> *cancel) {
+    const int64_t d = mat_->d, dpad = mat_->dpad;
+    status = LRA_OK;
+    float *S = ws_.S, *W = ws_.W;
+    gaussian(s_, stream_key(seed, LRA_STREAM_INIT, 0, 0), d, dpad, p, S);
+    lra_status st = cholqr2(S, p);
+    if (st != LRA_OK) return st;
+    E.clear();
+    ell = 0;
+    const int PP = pad_p(p);
+    double *h = ws_.host;
+    while (true) {
+        ritz(S, p, false, 1, o.warm_start != 0);
+        LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
+        sync();
+        if (ell > 0 && (st = qr_status()) != LRA_OK) return st;  // the previous step's CholeskyQR2
+        double sk = 0.0;
+        for (int j = 0; j < k; ++j) sk += h[j];
+        E.push_back(mat_->fro2 - sk);
+        if (o.trace_E && (int)E.size() <= o.trace_cap) o.trace_E[E.size() - 1] = E.back();
+        const double rf = r_floor >= 0.0 ? r_floor : theory_rate(lam, h, k, p);
+        if (outer_stop(E, eps, ell, o.min_outer, rf)) break;
+        if (ell >= o.max_outer) {
+            status = LRA_ENOTCONV;
+            break;
+        }
+        if (cancel && cancel->load()) return LRA_ECANCELLED;
+        const float *G0 = nullptr;
+        if (o.warm_start) {
+            // Move the basis onto the Ritz vectors, S <- S V (same span, so the
+            // same Algorithm 1 step; the next Rayleigh-Ritz matrix is then
+            // nearly diagonal and the eigensolver's sweeps stop early).  Warm
+            // start in that basis: W0 = S V diag(1/(lam - rho)); the first
+            // anchor's X X^T W0 = (X Q) V diag(1/(lam - rho)) with X Q from the
+            // Rayleigh-Ritz step: a d x p product.
+            if (timer) timer->begin(KernelTimer::WARM, p);
+            evecs_to_rm(s_, ws_.evecs, p, p, ws_.P);
+            apply_right(s_, S, dpad, 1, dpad, p, ws_.P, p, W, 1, dpad);
+            LRA_CUDA(cudaMemcpyAsync(S, W, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
+            shift_scale_cols(s_, S, W, dpad, dpad, p, ws_.evals, lam);
+            ritz_scaled(s_, ws_.evecs, ws_.evals, p, lam, ws_.P);
+            apply_right(s_, ws_.T1, dpad, 1, dpad, p, ws_.P, p, ws_.Gp, PP, 1);
+            if (timer) timer->end();
+            G0 = ws_.Gp;
+        } else {
+            LRA_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * dpad * p, s_));
+        }
+        SolveInfo info;
+        st = solve_linear(S, W, p, lam, mu, l1up, seed, solve_count, o, G0, info);
+        if (st != LRA_OK) return st;
+        R.eta = info.eta;
+        R.m = info.m;
+        R.last_residual = info.residual;
+        std::swap(S, W);
+        cholqr2(S, p, true);
+        ++ell;
+    }
+    S_out = S;
+    return LRA_OK;
+}
+
 lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
                          double *ritz_out, lra_report *rep, const std::atomic<int> *cancel) {
     const auto t_all = std::chrono::steady_clock::now();
@@ -845,59 +1080,14 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     R.ms_shift = ms_since(t0);
 
     t0 = std::chrono::steady_clock::now();
-    float *S = ws_.S, *W = ws_.W;
-    gaussian(s_, stream_key(seed, LRA_STREAM_INIT, 0, 0), d, dpad, p, S);
-    lra_status st = cholqr2(S, p);
-    if (st != LRA_OK) return st;
+    float *S = nullptr;
     std::vector<double> E;
     int ell = 0;
-    const int PP = pad_p(p);
+    lra_status lst = LRA_OK;
+    lra_status st = loop_d(k, p, eps, seed, lam, mu, l1up, o, solve_count, -1.0, S, ell, E, lst, R, cancel);
+    if (st != LRA_OK) return st;
+    if (lst != LRA_OK) status = lst;
     double *h = ws_.host;
-    while (true) {
-        ritz(S, p, false, 1, o.warm_start != 0);
-        LRA_CUDA(cudaMemcpyAsync(h, ws_.evals, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
-        sync();
-        if (ell > 0 && (st = qr_status()) != LRA_OK) return st;  // the previous step's CholeskyQR2
-        double sk = 0.0;
-        for (int j = 0; j < k; ++j) sk += h[j];
-        E.push_back(mat_->fro2 - sk);
-        if (o.trace_E && (int)E.size() <= o.trace_cap) o.trace_E[E.size() - 1] = E.back();
-        if (outer_stop(E, eps, ell, o.min_outer, theory_rate(lam, h, k, p))) break;
-        if (ell >= o.max_outer) {
-            status = LRA_ENOTCONV;
-            break;
-        }
-        if (cancel && cancel->load()) return LRA_ECANCELLED;
-        const float *G0 = nullptr;
-        if (o.warm_start) {
-            // Move the basis onto the Ritz vectors, S <- S V (same span, so the
-            // same Algorithm 1 step; the next Rayleigh-Ritz matrix is then
-            // nearly diagonal and the eigensolver's sweeps stop early).  Warm
-            // start in that basis: W0 = S V diag(1/(lam - rho)); the first
-            // anchor's X X^T W0 = (X Q) V diag(1/(lam - rho)) with X Q from the
-            // Rayleigh-Ritz step: a d x p product.
-            if (timer) timer->begin(KernelTimer::WARM, p);
-            evecs_to_rm(s_, ws_.evecs, p, p, ws_.P);
-            apply_right(s_, S, dpad, 1, dpad, p, ws_.P, p, W, 1, dpad);
-            LRA_CUDA(cudaMemcpyAsync(S, W, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
-            shift_scale_cols(s_, S, W, dpad, dpad, p, ws_.evals, lam);
-            ritz_scaled(s_, ws_.evecs, ws_.evals, p, lam, ws_.P);
-            apply_right(s_, ws_.T1, dpad, 1, dpad, p, ws_.P, p, ws_.Gp, PP, 1);
-            if (timer) timer->end();
-            G0 = ws_.Gp;
-        } else {
-            LRA_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * dpad * p, s_));
-        }
-        SolveInfo info;
-        st = solve_linear(S, W, p, lam, mu, l1up, seed, solve_count, o, G0, info);
-        if (st != LRA_OK) return st;
-        R.eta = info.eta;
-        R.m = info.m;
-        R.last_residual = info.residual;
-        std::swap(S, W);
-        cholqr2(S, p, true);
-        ++ell;
-    }
     R.outer_iters = ell;
     R.ms_outer = ms_since(t0);
 

@@ -85,6 +85,8 @@ struct Opts {
     double acc_theta = 0.5;
     int acc_max_outer = 200;
     int64_t acc_target = 0;    // samples per epoch the proximal weight aims for; 0 = n
+    int partition = 0;         // 1: Algorithm 6 with adaptive partitioning and deflation
+    int part_max_iters = 2000; // cap on Algorithm 3's iteration count
 };
 
 // CUDA-event timing of individual kernel launches on the engine's stream.
@@ -187,6 +189,10 @@ struct Workspace {
 };
 
 size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items = -1);
+
+// Algorithm 6 with adaptive partitioning and deflation (partition.cu)
+lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
+                             double *ritz, lra_report *rep);
 // the sp_items argument of a workspace for X products on `m`
 inline int64_t ws_items(const lra_mat *m) { return m->sp ? m->sp->nitems : -1; }
 
@@ -243,6 +249,29 @@ class Engine {
     lra_status delta_estimate(int k, int p, uint64_t seed, double &delta);
     lra_status solve(int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
                      double *ritz, lra_report *rep, const std::atomic<int> *cancel);
+    // Algorithm 1 on D = (lam I - A)^{-1} with p columns from the Gaussian start
+    // (seed, INIT) and Rayleigh-Ritz with A every iteration, stopped on E_l with
+    // k target columns and the rate floor r_floor (< 0: from the Ritz values).
+    // Hard errors are returned; `status` is LRA_OK or LRA_ENOTCONV.  On return
+    // S points at the final basis (ws.S or ws.W) and ws.evals / ws.evecs hold
+    // its Ritz pairs with A.
+    lra_status loop_d(int k, int p, double eps, uint64_t seed, double lam, double mu, double l1up,
+                      const Opts &o, int64_t &solve_count, double r_floor, float *&S, int &ell,
+                      std::vector<double> &E, lra_status &status, lra_report &R,
+                      const std::atomic<int> *cancel);
+    // Algorithm 3 on A with kk vectors: L = min(ceil(eps^-1 ln(d/eps)), cap) block
+    // power steps from the start (seed, BLOCK, 0), then the Ritz values (host, desc)
+    lra_status alg3_a(int kk, double eps, int cap, uint64_t seed, double *vals, int &iters);
+    // Algorithm 3 on D = (lam I - A)^{-1} with kk vectors from (seed, BLOCK, 2),
+    // every product a solve warm-started by the previous iteration's Galerkin
+    // projection; values are eigenvalue estimates of D (host, desc)
+    lra_status alg3_d(int kk, double eps, int cap, uint64_t seed, double lam, double mu, double l1up,
+                      double l1hat, const Opts &o, int64_t &solve_count, double *vals, int &iters);
+    // Algorithm 1 on A with b columns (no oversampling) from (seed, BLOCK, 1),
+    // Rayleigh-Ritz with A every iteration, stopped on E with rate floor r_floor;
+    // the Ritz vectors are left in ws.U (b columns), values in ws.host[0..b)
+    lra_status power_block(int b, double eps, double r_floor, uint64_t seed, const Opts &o, int &iters,
+                           lra_status &status);
 
     void sync();
     void check_tc();  // raise if a tensor-core kernel reported a timed-out wait

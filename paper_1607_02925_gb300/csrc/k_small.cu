@@ -807,6 +807,30 @@ void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const _
     LRA_LAUNCHED();
 }
 
+namespace {
+__global__ void copy_full_kernel(const double *__restrict__ C, int p, int p4, double *__restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p * p) return;
+    const int a = e % p, b = e / p;
+    out[e] = C[a * p4 + b];
+}
+}  // namespace
+
+void cross_full(cudaStream_t s, const float *A, const float *B, int64_t rows, int64_t ld, int p, double *out,
+                double *scratch) {
+    const int p4 = (int)round_up(p, 4);
+    const int nb = gram_blocks(rows);
+    const size_t smem = sizeof(float) * 2 * kGR * p4;
+    ensure_smem(cross_gram_kernel, (int)smem);
+    cross_gram_kernel<<<nb, 256, smem, s>>>(A, nullptr, nullptr, B, rows, ld, p, p4, scratch);
+    LRA_LAUNCHED();
+    double *C = scratch + (int64_t)nb * p4 * p4;
+    cross_reduce_kernel<<<(unsigned)ceil_div(p4 * p4, 256), 256, 0, s>>>(scratch, nb, p4, C);
+    LRA_LAUNCHED();
+    copy_full_kernel<<<(unsigned)ceil_div(p * p, 256), 256, 0, s>>>(C, p, p4, out);
+    LRA_LAUNCHED();
+}
+
 void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc) {
     ortho_correct_kernel<<<p, (unsigned)round_up(p, 32), 0, s>>>(H, G, p, Hc);
     LRA_LAUNCHED();

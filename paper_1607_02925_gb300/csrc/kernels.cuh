@@ -94,6 +94,9 @@ void gram64(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_
 // scratch >= gram_scratch(p) doubles
 void cross_gram(cudaStream_t s, const float *A, const __nv_bfloat16 *Ah, const __nv_bfloat16 *Al, const float *B,
                 int64_t rows, int64_t ld, int p, double *H, double *scratch);
+// out (p x p FP64 column-major) = A^T B for A, B rows x p column-major (leading dim ld)
+void cross_full(cudaStream_t s, const float *A, const float *B, int64_t rows, int64_t ld, int p, double *out,
+                double *scratch);
 // Hc = 2H - (G H + H G)/2: Rayleigh-Ritz matrix of the orthonormalised basis
 // to first order in G - I (all p x p FP64 column-major, symmetric)
 void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc);

@@ -1,0 +1,268 @@
+// Algorithm 6 with adaptive partitioning of {1..k} and deflation (Sec. 3:
+// Algorithms 3, 4, 5, 6, 7).  Stage t, starting at index s with the columns
+// u_1..u_{s-1} found so far, works on the deflated matrix
+// X_{-(s-1)} = (I - U U^T) X, formed explicitly (Sec. 3 assumes the projection
+// already applied to X's columns) as a dense matrix of the original storage,
+// so that every stage runs the same kernels as the q = k path:
+//   Algorithm 3 on A_{-(s-1)} (k - s + 1 vectors, eps' = 1/(9 p^2));
+//   Algorithm 4: the first multiplicative gap -> Algorithm 1 on A_{-(s-1)}
+//   with q - s + 1 columns; otherwise Algorithm 7 (the shift), Algorithm 3 on
+//   D_{-(s-1)} = (lam I - A_{-(s-1)})^{-1} (eps' = 1/(9p)), Algorithm 5 (the
+//   first additive gap >= 5 Delta / 9, else k) and Algorithm 1 on D_{-(s-1)}
+//   with p' = q - s + 1 columns (q < k) or p - (s - 1) (q = k, oversampled);
+//   s = q + 1.
+// The columns are orthonormalised together (CholeskyQR2) and Algorithm 2 with
+// X X^T on the exact FP32 values returns U.
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "engine.h"
+
+namespace lra {
+
+namespace {
+
+constexpr int kDT = 32;  // deflation tile: 32 rows x 32 columns
+
+// out[r + i ldo] = X[r + i ldx] - sum_a U[r + a ldu] Y[i PP + a] for r < rows,
+// i < n (X == nullptr: 0 - ...); U is column-major, Y = X^T U row-major n x PP.
+template <typename TX>
+__global__ void __launch_bounds__(256) deflate_kernel(const TX *__restrict__ X, int64_t ldx,
+                                                      const float *__restrict__ U, int64_t ldu, int c,
+                                                      const float *__restrict__ Y, int PP, int64_t rows,
+                                                      int64_t n, float *__restrict__ out, int64_t ldo) {
+    extern __shared__ float dsm[];
+    const int cs = c + 1;
+    float *Us = dsm, *Ys = dsm + kDT * cs;
+    const int64_t i0 = (int64_t)blockIdx.x * kDT, r0 = (int64_t)blockIdx.y * kDT;
+    for (int e = threadIdx.x; e < kDT * c; e += 256) {
+        const int rr = e % kDT, a = e / kDT;
+        const int64_t r = r0 + rr;
+        Us[rr * cs + a] = r < rows ? U[r + (int64_t)a * ldu] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < kDT * c; e += 256) {
+        const int a = e % c, ii = e / c;
+        const int64_t i = i0 + ii;
+        Ys[ii * cs + a] = i < n ? Y[i * PP + a] : 0.0f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r = r0 + tx;
+    if (r >= rows) return;
+    for (int jj = 0; jj < kDT / 8; ++jj) {
+        const int ii = ty * (kDT / 8) + jj;
+        const int64_t i = i0 + ii;
+        if (i >= n) break;
+        float acc = 0.0f;
+        for (int a = 0; a < c; ++a) acc = fmaf(Us[tx * cs + a], Ys[ii * cs + a], acc);
+        const float x = X ? to_f32(X[r + i * ldx]) : 0.0f;
+        out[r + i * ldo] = x - acc;
+    }
+}
+
+// out[rowidx[e] + i ldo] += val[e] for the entries e of compressed column i
+__global__ void csc_add_kernel(const int64_t *__restrict__ colptr, const int32_t *__restrict__ rowidx,
+                               const float *__restrict__ val, int64_t n, float *__restrict__ out, int64_t ldo) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    for (int64_t e = colptr[i] + (threadIdx.x & 31); e < colptr[i + 1]; e += 32)
+        out[rowidx[e] + i * ldo] += val[e];
+}
+
+void deflate(cudaStream_t s, const lra_mat *m, const float *U, int c, const float *Y, int PP, float *out) {
+    const int64_t rows = m->dpad, n = m->n;
+    const dim3 grid((unsigned)ceil_div(n, kDT), (unsigned)ceil_div(rows, kDT));
+    const size_t smem = sizeof(float) * 2 * kDT * (c + 1);
+    if (m->sp) {
+        deflate_kernel<float><<<grid, 256, smem, s>>>(nullptr, 0, U, rows, c, Y, PP, rows, n, out, rows);
+        LRA_LAUNCHED();
+        csc_add_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(m->sp->colptr, m->sp->rowidx, m->sp->cval, n, out,
+                                                               rows);
+        LRA_LAUNCHED();
+    } else if (m->storage == LRA_BF16) {
+        deflate_kernel<__nv_bfloat16><<<grid, 256, smem, s>>>(static_cast<const __nv_bfloat16 *>(m->X), rows, U,
+                                                              rows, c, Y, PP, rows, n, out, rows);
+        LRA_LAUNCHED();
+    } else {
+        deflate_kernel<float><<<grid, 256, smem, s>>>(m->X32, rows, U, rows, c, Y, PP, rows, n, out, rows);
+        LRA_LAUNCHED();
+    }
+}
+
+struct MatGuard {
+    lra_mat *m = nullptr;
+    ~MatGuard() {
+        if (m) lra_mat_destroy(m);
+    }
+};
+
+// Algorithm 4: offset j of the first q = s + j in I \ {k} with
+// lam_hat[j + 1] <= lam_hat[j] (1 - p^-2), or -1
+int alg4(const double *lam_hat, int kk, int p) {
+    for (int j = 0; j + 1 < kk; ++j)
+        if (lam_hat[j + 1] <= lam_hat[j] * (1.0 - 1.0 / ((double)p * p))) return j;
+    return -1;
+}
+
+// Algorithm 5: offset of the first q in I \ {k} with inv[j + 1] - inv[j] >=
+// 5 Delta / 9 (inv = estimates of lam - lambda_i), else kk - 1 (q = k)
+int alg5(const double *inv, int kk, double delta) {
+    for (int j = 0; j + 1 < kk; ++j)
+        if (inv[j + 1] - inv[j] >= 5.0 * delta / 9.0) return j;
+    return kk - 1;
+}
+
+}  // namespace
+
+lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t seed, const Opts &o, float *U_out,
+                             double *ritz_out, lra_report *rep) {
+    const auto t_all = std::chrono::steady_clock::now();
+    const int64_t launches0 = launches_of_thread();
+    lra_ctx *ctx = mat->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t d = mat->d, dpad = mat->dpad, n = mat->n;
+    lra_report R;
+    std::memset(&R, 0, sizeof(R));
+    R.struct_size = sizeof(R);
+
+    // the original matrix's workspace: Delta, the columns found, the deflation
+    // products and the final Rayleigh-Ritz step
+    Workspace ws0(ctx, dpad, n, p + 1, nullptr, ws_items(mat));
+    Engine e0(mat, ws0, s);
+    e0.ensure_table(o.sampling);
+    R.fro2 = mat->fro2;
+    double delta = o.delta;
+    if (!(delta > 0)) {
+        const lra_status st = e0.delta_estimate(k, p, seed, delta);
+        if (st != LRA_OK) return st;
+    }
+    R.delta = delta;
+    float *Ucols = static_cast<float *>(dev_alloc(ctx, sizeof(float) * dpad * p));
+    struct Free {
+        lra_ctx *c;
+        void *p;
+        size_t b;
+        ~Free() { dev_free(c, p, b); }
+    } free_u{ctx, Ucols, sizeof(float) * dpad * p};
+    LRA_CUDA(cudaMemsetAsync(Ucols, 0, sizeof(float) * dpad * p, s));
+
+    lra_status status = LRA_OK;
+    int s_idx = 1, t = 0, ncols = 0;
+    std::vector<double> lam_hat(k + 1), theta(k + 1), inv(k + 1);
+    while (s_idx <= k) {
+        ++t;
+        const uint64_t seed_t = stream_key(seed, LRA_STREAM_PART, (uint64_t)t, 0);
+        const int kk = k - s_idx + 1;
+        MatGuard defl;
+        lra_mat *cur = mat;
+        if (s_idx > 1) {
+            // X_{-(s-1)} = X - U (X^T U)^T, then a matrix of the original storage
+            const int PP = pad_p(ncols);
+            e0.xt_mul(Ucols, ncols, ws0.Y, false);
+            float *tmp = static_cast<float *>(dev_alloc(ctx, sizeof(float) * dpad * n));
+            deflate(s, mat, Ucols, ncols, ws0.Y, PP, tmp);
+            LRA_CUDA(cudaStreamSynchronize(s));
+            const lra_dtype storage = mat->sp ? LRA_F32 : mat->storage;
+            const lra_status st = lra_create_dense(ctx, d, n, LRA_F32, tmp, dpad, 1, storage, &defl.m);
+            dev_free(ctx, tmp, sizeof(float) * dpad * n);
+            if (st != LRA_OK) return st;
+            cur = defl.m;
+        }
+        Workspace ws(ctx, cur->dpad, cur->n, p, nullptr, ws_items(cur));
+        Engine e(cur, ws, s);
+        e.ensure_table(o.sampling);
+        int it3 = 0;
+        lra_status st = e.alg3_a(kk, 1.0 / (9.0 * p * p), o.part_max_iters, seed_t, lam_hat.data(), it3);
+        if (st != LRA_OK) return st;
+        const int j = alg4(lam_hat.data(), kk, p);
+        int q, keep, iters = 0, kind;
+        lra_status bst = LRA_OK;
+        const float *cols = nullptr;
+        if (j >= 0) {
+            kind = 1;
+            q = s_idx + j;
+            keep = j + 1;
+            const double rf = (lam_hat[j + 1] / lam_hat[j]) * (lam_hat[j + 1] / lam_hat[j]);
+            st = e.power_block(keep, eps, rf, seed_t, o, iters, bst);
+            if (st != LRA_OK) return st;
+            cols = ws.U;
+        } else {
+            kind = 2;
+            int64_t solve_count = 0;
+            const double l1hat = e.lambda1_estimate(seed_t);
+            const double l1up = l1hat / (1.0 - 0.25);
+            double lam = 0, inv1 = 0, mu = 0;
+            int rounds = 0;
+            st = e.shift_tune(seed_t, l1hat, delta, o, solve_count, lam, inv1, mu, rounds, nullptr);
+            if (st == LRA_EDIVERGED) return st;
+            int itd = 0;
+            st = e.alg3_d(kk, 1.0 / (9.0 * p), o.part_max_iters, seed_t, lam, mu, l1up, l1hat, o, solve_count,
+                          theta.data(), itd);
+            if (st != LRA_OK) return st;
+            for (int i = 0; i < kk; ++i) inv[i] = 1.0 / theta[i];
+            const int jj = alg5(inv.data(), kk, delta);
+            q = s_idx + jj;
+            const int pp = q == k ? p - (s_idx - 1) : q - s_idx + 1;
+            keep = q == k ? pp : q - s_idx + 1;
+            // rate floor of a block without oversampling, from Algorithm 3 on D
+            const double rf = q == k ? -1.0 : (inv[jj] / inv[jj + 1]) * (inv[jj] / inv[jj + 1]);
+            float *S = nullptr;
+            std::vector<double> E;
+            st = e.loop_d(q - s_idx + 1, pp, eps, seed_t, lam, mu, l1up, o, solve_count, rf, S, iters, E, bst, R,
+                          nullptr);
+            if (st != LRA_OK) return st;
+            // Ritz vectors S V[:, :keep] into ws.U
+            evecs_to_rm(s, ws.evecs, pp, keep, ws.P);
+            apply_right(s, S, cur->dpad, 1, cur->dpad, pp, ws.P, keep, ws.U, 1, cur->dpad);
+            cols = ws.U;
+            R.shift_rounds += rounds;
+            R.lambda = lam;
+            R.mu_lb = mu;
+        }
+        if (bst != LRA_OK) status = bst;
+        R.outer_iters += iters;
+        R.solves += e.stats.solves;
+        R.epochs += e.stats.epochs;
+        R.inner_steps += e.stats.inner_steps;
+        R.x_passes += e.stats.x_passes;
+        if (t <= LRA_MAX_P) {
+            R.part_q[t - 1] = q;
+            R.part_kind[t - 1] = kind;
+        }
+        R.part_stages = t;
+        // append and orthonormalise all columns found so far
+        LRA_CUDA(cudaMemcpyAsync(Ucols + (size_t)ncols * dpad, cols, sizeof(float) * dpad * keep,
+                                 cudaMemcpyDeviceToDevice, s));
+        ncols += keep;
+        st = e0.cholqr2(Ucols, ncols);
+        if (st != LRA_OK) return st;
+        s_idx = q + 1;
+    }
+    // Algorithm 2 with X X^T on the p columns (exact FP32 values of X)
+    e0.ritz(Ucols, p, true);
+    evecs_to_rm(s, ws0.evecs, p, k, ws0.P);
+    apply_right(s, Ucols, dpad, 1, dpad, p, ws0.P, k, ws0.U, 1, dpad);
+    LRA_CUDA(cudaMemcpy2DAsync(U_out, sizeof(float) * d, ws0.U, sizeof(float) * dpad, sizeof(float) * d, k,
+                               cudaMemcpyDefault, s));
+    LRA_CUDA(cudaMemcpyAsync(ritz_out, ws0.evals, sizeof(double) * k, cudaMemcpyDefault, s));
+    LRA_CUDA(cudaMemcpyAsync(ws0.host, ws0.evals, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    LRA_CUDA(cudaStreamSynchronize(s));
+    double sk = 0.0;
+    for (int j = 0; j < k; ++j) sk += ws0.host[j];
+    R.err_est = mat->fro2 - sk;
+    R.solves += e0.stats.solves;
+    R.x_passes += e0.stats.x_passes;
+    R.status = status;
+    R.kernel_launches = launches_of_thread() - launches0;
+    R.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_all).count();
+    if (rep) {
+        const size_t sz = std::min(rep->struct_size ? rep->struct_size : sizeof(R), sizeof(R));
+        std::memcpy(rep, &R, sz);
+        rep->struct_size = sz;
+    }
+    return status;
+}
+
+}  // namespace lra
