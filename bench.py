@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=1, help="samples per SVRG inner step (power of two <= 16)")
     ap.add_argument("--acc", action="store_true", help="accelerated SVRG solves (proximal-point loop)")
     ap.add_argument("--acc-target", type=int, default=0, help="samples per epoch of an accelerated subproblem (0 = n)")
+    ap.add_argument("--partition", action="store_true",
+                    help="Algorithm 6 with adaptive partitioning and deflation (all branches)")
     ap.add_argument("--serve", action="store_true", help="request-loop benchmark instead")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mean-ms", type=float, default=20.0)
@@ -198,6 +200,19 @@ def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
     r = O.solve(X64, wl.k, wl.p, args.eps, args.seed, o, lam1_hat=lh)
     t_outer = time.perf_counter() - t0
     return t_fixed, t_outer / max(outer_sample, 1), r.lam, r.E_trace
+
+
+def oracle_partition(wl, Xt_host, args, delta, threads):
+    """Seconds of one full FP64 oracle run of Algorithm 6 (adaptive partitioning
+    and deflation) on the same X, seed and Delta."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    from oracle import lra_oracle as O
+    from oracle import lra_partition as P
+    o = O.Options(tau=1e-3 if args.storage == "bf16" else 1e-5, batch=args.batch, acc=int(args.acc),
+                  acc_target=args.acc_target)
+    t0 = time.perf_counter()
+    P.adaptive_solve(O.as64(Xt_host), wl.k, wl.p, args.eps, args.seed, o, delta=delta)
+    return time.perf_counter() - t0
 
 
 def predicted_outer(wl, lam, E_trace, eps):
@@ -363,12 +378,17 @@ def run_reference(args):
     vals = []
     sample_desc = None
     for i in range(args.warmup + args.steps):
-        t_fixed, t_outer, lam, E = oracle_sample(wl, Xh, args, lam1, args.cpu_sample_outer, threads)
-        Lstar = predicted_outer(wl, lam, E, args.eps)
-        v = t_fixed + t_outer * Lstar
-        sample_desc = (f"FP64 oracle on the same X and seeds: lambda_1 estimate + "
-                       f"{args.cpu_sample_outer} outer iterations, extrapolated to {Lstar} outer "
-                       f"iterations (sampled Ritz error, theory rate)")
+        if args.partition:
+            _, lk, lp1 = spectrum(wl)
+            v = oracle_partition(wl, Xh, args, (lk - lp1) / 1.5, threads)
+            sample_desc = "FP64 oracle's Algorithm 6 on the same X, seed and Delta: one full solve per step"
+        else:
+            t_fixed, t_outer, lam, E = oracle_sample(wl, Xh, args, lam1, args.cpu_sample_outer, threads)
+            Lstar = predicted_outer(wl, lam, E, args.eps)
+            v = t_fixed + t_outer * Lstar
+            sample_desc = (f"FP64 oracle on the same X and seeds: lambda_1 estimate + "
+                           f"{args.cpu_sample_outer} outer iterations, extrapolated to {Lstar} outer "
+                           f"iterations (sampled Ritz error, theory rate)")
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
@@ -405,7 +425,7 @@ def run_lra(args):
     delta = (lk - lp1) / 1.5
     pol = lra.LRA_SHIFT_FAR if args.shift == "far" else lra.LRA_SHIFT_PAPER
     opt = lra.options(shift_policy=pol, delta=delta, profile=1, batch=args.batch, acc=int(args.acc),
-                      acc_target=args.acc_target)
+                      acc_target=args.acc_target, partition=int(args.partition))
     if args.max_outer > 0:
         opt.max_outer = args.max_outer
 
@@ -527,7 +547,12 @@ def run_lra(args):
                "d2h_bytes_per_step": wl.d * wl.k * 4 + wl.k * 8}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.partition:
+        threads = len(os.sched_getaffinity(0))
+        t_full = oracle_partition(wl, src.oracle_input(), args, delta, threads)
+        cpu = {"value": t_full, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": "FP64 oracle's Algorithm 6 on the same X, seed and Delta: one full solve"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
         t_fixed, t_outer, lam, E = oracle_sample(wl, src.oracle_input(), args, None, args.cpu_sample_outer,
                                                  threads)
@@ -548,11 +573,13 @@ def run_lra(args):
             "dtype": "f32" if storage_name == "csr" else args.storage, "data": "synthetic",
             "config": {"workload": args.workload, "d": wl.d, "n": wl.n, "k": wl.k, "p": wl.p,
                        "storage": storage_name, "shift": args.shift, "eps": args.eps, "batch": args.batch,
-                       "acc": bool(args.acc),
+                       "acc": bool(args.acc), "partition": bool(args.partition),
                        "l2": "inputs larger than L2 (X %.2f GB per pass)" % (src.x_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": {"ratio_err_over_opt": ratio, "outer_iters": last.outer_iters,
                          "status": reps[-1][0]},
+            "partition_stages": ([[int(last.part_q[t]), "power" if last.part_kind[t] == 1 else "shift"]
+                                  for t in range(last.part_stages)] if args.partition else None),
             "roofline": roof,
             "clocks": clk,
             "e2e": e2e,

@@ -400,9 +400,9 @@ class Context:
         ||M||_F <= tau ||B||_F (or after `fixed_epochs` anchors); otherwise m
         inner steps on the stream (seed, SVRG, solve, e).  Stalls (an epoch that
         shrinks the residual by less than 10% after the third) end the solve at
-        its floor; a residual above both 10x the best and the first one is
-        divergence (a rebound at the rounding floor, far below the start, is a
-        stall).
+        its floor; a residual above 10x the best, above the first one and above
+        1e-3 is divergence (a rebound at the rounding floor, below the start or
+        below 1e-3 ||B||, is left to the stall rule).
 
         With `acc` (one subproblem of acc_svrg_solve) the solve first checks the
         original system's residual at the epoch-0 anchor and returns at once
@@ -430,7 +430,7 @@ class Context:
             self.epochs += 1
             if e == 0:
                 res0 = res
-            if not np.isfinite(res) or (res > 10.0 * best and res > res0):
+            if not np.isfinite(res) or (res > 10.0 * best and res > max(res0, 1e-3)):
                 st.status = "diverged"
                 return W, st
             tol = o.tau

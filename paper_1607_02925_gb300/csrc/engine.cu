@@ -94,7 +94,7 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
     const int PP = pad_p(pmax);
     const int nch = sp_items >= 0 ? 1 : std::max(xy_chunks(dpad, n, 128), xy_chunks(dpad, n, 256));
     size_t b = 0;
-    b += 9 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U, accelerated solve: Za Ra Wo
+    b += 8 * sizeof(float) * dpad * pmax;       // S W Wt M T1 U, accelerated solve: Za Wo
     b += sizeof(float) * dpad * PP;             // Wr
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
@@ -125,7 +125,6 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         T1 = alloc<float>(blk);
         U = alloc<float>(blk);
         Za = alloc<float>(blk);
-        Ra = alloc<float>(blk);
         Wo = alloc<float>(blk);
         Wr = alloc<float>((size_t)dpad * PPmax);
         Q = alloc<float>((size_t)n * PPmax);
@@ -147,7 +146,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         LRA_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
         Gm = alloc<double>(pp);
         norms = alloc<double>(4);
-        epi = alloc<double>(2 * (dpad / 16) + 8);
+        epi = alloc<double>(3 * (dpad / 16) + 8);
         dots = alloc<double>(pmax + 4);
         Rinv = alloc<float>(pp);
         P = alloc<float>(pp);
@@ -386,7 +385,7 @@ void Engine::a_apply(const float *W, int p, float *G) {
 }
 
 void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
-                    double *nM2, double *nB2) {
+                    double *nM2, double *nB2, const AccHook *acc, double *nR2) {
     const int PP = pad_p(p);
     const float *Gsrc = ws_.Gp;
     int nch = 0;
@@ -402,14 +401,16 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
     }
     if (!G0) nch = ws_.nch;
     if (timer) timer->begin(KernelTimer::EPI, p);
-    anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi);
+    anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi, acc ? acc->Z : nullptr,
+                    acc ? acc->gamma : 0.0);
     if (timer) timer->end();
     if (nM2 || nB2) {
-        LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+        LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, (acc ? 3 : 2) * sizeof(double), cudaMemcpyDeviceToHost, s_));
         if (tc(false)) check_tc();
         sync();
         if (nM2) *nM2 = ws_.host[0];
         if (nB2) *nB2 = ws_.host[1];
+        if (acc && nR2) *nR2 = ws_.host[2];
     }
 }
 
@@ -532,16 +533,16 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
     double best = INFINITY, prev = INFINITY, res0 = INFINITY;
     for (int e = 0; e < max_e; ++e) {
         LRA_CUDA(cudaMemcpyAsync(ws_.Wt, W, blk, cudaMemcpyDeviceToDevice, s_));
-        double nM2, nB2;
-        anchor(ws_.Wt, B, p, lam, ws_.M, (e == 0) ? G0 : nullptr, &nM2, &nB2);
+        double nM2, nB2, nR2 = 0.0;
+        anchor(ws_.Wt, B, p, lam, ws_.M, (e == 0) ? G0 : nullptr, &nM2, &nB2, acc, &nR2);
         stats.epochs += 1;
         const double res = nB2 > 0 ? std::sqrt(nM2 / nB2) : 0.0;
         info.epochs = e + 1;
         info.residual = res;
         if (e == 0) res0 = res;
-        // divergence: above 10x the best and above the start (a rebound at the
-        // rounding floor, far below the start, is left to the stall rule)
-        if (!std::isfinite(res) || (res > 10.0 * best && res > res0)) {
+        // divergence: above 10x the best, above the start and above 1e-3 (a
+        // rebound at the rounding floor is left to the stall rule)
+        if (!std::isfinite(res) || (res > 10.0 * best && res > std::max(res0, 1e-3))) {
             set_error("SVRG: residual " + std::to_string(res) + " after a best of " + std::to_string(best) +
                       " at epoch " + std::to_string(e) + " (lambda " + std::to_string(lam) + ", mu " +
                       std::to_string(mu) + ", p " + std::to_string(p) + ")");
@@ -551,13 +552,9 @@ lra_status Engine::svrg_solve(const float *B, float *W, int p, double lam, doubl
         double tol = o.tau;
         if (acc) {
             if (e == 0) {
-                // the original system's residual at W: M - gamma (W - Z)
-                acc_resid(s_, ws_.M, ws_.Wt, acc->Z, mat_->dpad, mat_->dpad, p, acc->gamma, ws_.dots);
-                LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.dots, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
-                sync();
-                double r2 = 0.0;
-                for (int j = 0; j < p; ++j) r2 += ws_.host[j];
-                info.outer_res = std::sqrt(r2);
+                // the original system's residual at W, (lam - gamma) W - X X^T W - B,
+                // summed by the anchor's epilogue
+                info.outer_res = std::sqrt(nR2);
                 if (o.fixed_epochs <= 0 && info.outer_res <= o.tau * acc->nB) {
                     info.outer_done = true;
                     return LRA_OK;
@@ -622,7 +619,7 @@ lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double
     const double q = mu / (mu + gamma), sq = std::sqrt(q), beta = (1.0 - sq) / (1.0 + sq);
     const int64_t dpad = mat_->dpad;
     col_dots(s_, B, B, dpad, dpad, p, ws_.dots);
-    acc_extrapolate(s_, W, ws_.Wo, ws_.Za, ws_.Ra, B, dpad, dpad, p, 0.0f, (float)gamma, true);
+    acc_extrapolate(s_, W, ws_.Wo, ws_.Za, dpad, dpad, p, 0.0f, true);
     LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.dots, sizeof(double) * p, cudaMemcpyDeviceToHost, s_));
     sync();
     double b2 = 0.0;
@@ -637,7 +634,9 @@ lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double
     std::vector<double> hist;
     for (int s = 0; s < o.acc_max_outer; ++s) {
         SolveInfo sub;
-        const lra_status st = svrg_solve(ws_.Ra, W, p, lam + gamma, mu + gamma, l1up, seed, solve_count++, o,
+        // the subproblem's right-hand side B + gamma Z is formed inside the anchor's
+        // epilogue (FP64), from B and Z
+        const lra_status st = svrg_solve(B, W, p, lam + gamma, mu + gamma, l1up, seed, solve_count++, o,
                                          s == 0 ? G0 : nullptr, sub, &hook);
         info.epochs += sub.epochs;
         info.inner_steps += sub.inner_steps;
@@ -660,7 +659,7 @@ lra_status Engine::acc_solve(const float *B, float *W, int p, double lam, double
             info.status = LRA_OK;
             return LRA_OK;
         }
-        acc_extrapolate(s_, W, ws_.Wo, ws_.Za, ws_.Ra, B, dpad, dpad, p, (float)beta, (float)gamma, false);
+        acc_extrapolate(s_, W, ws_.Wo, ws_.Za, dpad, dpad, p, (float)beta, false);
     }
     return LRA_OK;
 }

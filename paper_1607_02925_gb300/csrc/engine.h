@@ -154,7 +154,7 @@ struct Workspace {
     double *H = nullptr, *Hc = nullptr, *evals = nullptr, *evecs = nullptr, *eigwork = nullptr, *gscr = nullptr;
     double *Gm = nullptr, *norms = nullptr, *epi = nullptr, *dots = nullptr;
     float *Rinv = nullptr, *P = nullptr;
-    float *Za = nullptr, *Ra = nullptr, *Wo = nullptr;  // accelerated solve: Z, B + gamma Z, previous W
+    float *Za = nullptr, *Wo = nullptr;  // accelerated solve: extrapolated point Z, previous W
     __nv_bfloat16 *Wb = nullptr, *Yb = nullptr;  // BF16 hi/lo operands of the tensor-core passes
     int64_t ldy = 0;
     int *status = nullptr;
@@ -210,8 +210,10 @@ class Engine {
     void x_mul(const float *Y, int p, float *G, bool use32);             // G dpad x p
     void a_apply(const float *W, int p, float *G);                       // G = X X^T W
     // G0 != nullptr: X X^T Wt precomputed (dpad x PP row-major), no X pass
+    // acc != nullptr: the subproblem anchor of an accelerated solve (B is the
+    // original right-hand side; M uses B + gamma Z; *nR2 = the original residual)
     void anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
-                double *nM2, double *nB2);
+                double *nM2, double *nB2, const struct AccHook *acc = nullptr, double *nR2 = nullptr);
     // m steps of `batch` samples (idx / cval hold m * batch entries)
     void inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
                const float *cval, int64_t m, double eta, double lam, int batch = 1);

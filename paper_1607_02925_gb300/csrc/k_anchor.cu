@@ -287,17 +287,26 @@ __global__ void __launch_bounds__(256) xy_kernel(const TX *__restrict__ X, int64
 
 // --- epilogue: M = lambda Wt - sum_c Gp[c] - B (or G only) -------------------
 // CTA = 16 rows x PP; four independent chunk accumulators per element, combined
-// in a fixed order (deterministic).
+// in a fixed order (deterministic).  With Z (a subproblem of the accelerated
+// solve, lambda = lambda_0 + gamma): M = lambda Wt - G - (B + gamma Z), and the
+// original residual r = lambda_0 Wt - G - B is summed as a third norm; both
+// are formed in FP64 from the FP32 inputs, so neither B + gamma Z nor the
+// cancellation M - gamma (Wt - Z) is rounded.  With Z (a subproblem of the accelerated
+// solve, lambda = lambda_0 + gamma): M = lambda Wt - G - (B + gamma Z), and the
+// original residual r = lambda_0 Wt - G - B is summed as a third norm; both
+// are formed in FP64 from the FP32 inputs, so neither B + gamma Z nor the
+// cancellation M - gamma (Wt - Z) is rounded.
 constexpr int kER = 16;
 
 __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__ Gp, int nchunks,
                                                        int64_t dpad, int PP, int p, double lam,
                                                        const float *__restrict__ Wt,
                                                        const float *__restrict__ B,
+                                                       const float *__restrict__ Z, double gamma,
                                                        float *__restrict__ out, int mode,
                                                        double *__restrict__ partial) {
     extern __shared__ __align__(16) float tile[];  // [kER][PP + 1]
-    __shared__ double red[2][8];
+    __shared__ double red[3][8];
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * kER;
     const int ts = PP + 1;
@@ -316,54 +325,61 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__
         tile[(e / PP) * ts + (e % PP)] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
-    double m2 = 0.0, b2 = 0.0;
+    double m2 = 0.0, b2 = 0.0, r2 = 0.0;
     for (int e = tid; e < kER * p; e += 256) {
         const int r = e % kER, j = e / kER;
         const int64_t gi = (r0 + r) + (int64_t)j * dpad;
         const float g = tile[r * ts + j];
         if (mode == 0) {
             const float b = B[gi];
-            const float m = (float)((double)lam * (double)Wt[gi] - (double)g - (double)b);
-            out[gi] = m;
-            m2 += (double)m * (double)m;
-            b2 += (double)b * (double)b;
+            if (Z) {
+                const double w = Wt[gi], z = Z[gi];
+                const double rr = (lam - gamma) * w - (double)g - (double)b;
+                const float m = (float)(rr + gamma * (w - z));
+                const double bb = (double)b + gamma * z;
+                out[gi] = m;
+                m2 += (double)m * (double)m;
+                b2 += bb * bb;
+                r2 += rr * rr;
+            } else {
+                const float m = (float)((double)lam * (double)Wt[gi] - (double)g - (double)b);
+                out[gi] = m;
+                m2 += (double)m * (double)m;
+                b2 += (double)b * (double)b;
+            }
         } else {
             out[gi] = g;
         }
     }
     if (mode == 0) {
+        const int ns = Z ? 3 : 2;
         m2 = warp_sum(m2);
         b2 = warp_sum(b2);
+        r2 = warp_sum(r2);
         if ((tid & 31) == 0) {
             red[0][tid >> 5] = m2;
             red[1][tid >> 5] = b2;
+            red[2][tid >> 5] = r2;
         }
         __syncthreads();
         if (tid == 0) {
-            double a0 = 0.0, a1 = 0.0;
-            for (int w = 0; w < 8; ++w) {
-                a0 += red[0][w];
-                a1 += red[1][w];
-            }
-            partial[2 * blockIdx.x] = a0;
-            partial[2 * blockIdx.x + 1] = a1;
+            double a[3] = {0.0, 0.0, 0.0};
+            for (int w = 0; w < 8; ++w)
+                for (int q = 0; q < ns; ++q) a[q] += red[q][w];
+            for (int q = 0; q < ns; ++q) partial[ns * blockIdx.x + q] = a[q];
         }
     }
 }
 
 // one warp: strided partial sums, then a fixed shuffle tree (deterministic)
-__global__ void norms_final_kernel(const double *__restrict__ partial, int nb, double *__restrict__ norms) {
-    double a0 = 0.0, a1 = 0.0;
-    for (int b = threadIdx.x; b < nb; b += 32) {
-        a0 += partial[2 * b];
-        a1 += partial[2 * b + 1];
-    }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    if (threadIdx.x == 0) {
-        norms[0] = a0;
-        norms[1] = a1;
-    }
+__global__ void norms_final_kernel(const double *__restrict__ partial, int nb, int ns,
+                                   double *__restrict__ norms) {
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += 32)
+        for (int q = 0; q < ns; ++q) a[q] += partial[ns * b + q];
+    for (int q = 0; q < 3; ++q) a[q] = warp_sum(a[q]);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < ns; ++q) norms[q] = a[q];
 }
 
 __global__ void pack_rm_kernel(const float *__restrict__ W, int64_t ldw, int64_t rows, int p, int PP,
@@ -462,14 +478,14 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
 
 void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
-                     double *scratch) {
+                     double *scratch, const float *Z, double gamma) {
     const int nb = (int)(dpad / kER);
     const size_t smem = sizeof(float) * kER * (PP + 1);
     const int mode = (Wt != nullptr) ? 0 : 1;
-    epilogue_kernel<<<nb, 256, smem, s>>>(Gp, nchunks, dpad, PP, p, lam, Wt, B, M, mode, scratch);
+    epilogue_kernel<<<nb, 256, smem, s>>>(Gp, nchunks, dpad, PP, p, lam, Wt, B, Z, gamma, M, mode, scratch);
     LRA_LAUNCHED();
     if (mode == 0 && norms) {
-        norms_final_kernel<<<1, 32, 0, s>>>(scratch, nb, norms);
+        norms_final_kernel<<<1, 32, 0, s>>>(scratch, nb, Z ? 3 : 2, norms);
         LRA_LAUNCHED();
     }
 }

@@ -707,59 +707,25 @@ __global__ void scale_block_kernel(float *__restrict__ A, int64_t rows, int64_t 
     A[r + j * ld] *= alpha;
 }
 
-// Accelerated solve: per column, sum over rows of (M - gamma (Wt - Z))^2, the
-// original system's residual (lambda I - A) Wt - B written through the
-// subproblem's anchor M = (lambda + gamma) Wt - A Wt - (B + gamma Z).
-__global__ void __launch_bounds__(256) acc_resid_kernel(const float *__restrict__ M,
-                                                        const float *__restrict__ Wt,
-                                                        const float *__restrict__ Z, int64_t rows,
-                                                        int64_t ld, double gamma, double *__restrict__ out) {
-    __shared__ double red[8];
-    const int j = blockIdx.x;
-    double s = 0.0;
-    for (int64_t r = threadIdx.x; r < rows; r += 256) {
-        const int64_t i = r + (int64_t)j * ld;
-        const double v = (double)M[i] - gamma * ((double)Wt[i] - (double)Z[i]);
-        s += v * v;
-    }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += red[w];
-        out[j] = t;
-    }
-}
-
-// Z = W + beta (W - Wold), Wold = W, R = B + gamma Z (first: Z = W, no Wold read).
+// Z = W + beta (W - Wold), Wold = W (first: Z = W, Wold not read).
 __global__ void acc_extrapolate_kernel(const float *__restrict__ W, float *__restrict__ Wold,
-                                       float *__restrict__ Z, float *__restrict__ R,
-                                       const float *__restrict__ B, int64_t rows, int64_t ld, int p,
-                                       float beta, float gamma, int first) {
+                                       float *__restrict__ Z, int64_t rows, int64_t ld, int p, float beta,
+                                       int first) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * p) return;
     const int j = (int)(e / rows);
     const int64_t i = e % rows + (int64_t)j * ld;
     const float w = W[i];
-    const float z = first ? w : w + beta * (w - Wold[i]);
+    Z[i] = first ? w : w + beta * (w - Wold[i]);
     Wold[i] = w;
-    Z[i] = z;
-    R[i] = B[i] + gamma * z;
 }
 
 }  // namespace
 
-void acc_resid(cudaStream_t s, const float *M, const float *Wt, const float *Z, int64_t rows, int64_t ld,
-               int p, double gamma, double *out) {
-    acc_resid_kernel<<<p, 256, 0, s>>>(M, Wt, Z, rows, ld, gamma, out);
-    LRA_LAUNCHED();
-}
-
-void acc_extrapolate(cudaStream_t s, const float *W, float *Wold, float *Z, float *R, const float *B,
-                     int64_t rows, int64_t ld, int p, float beta, float gamma, bool first) {
-    acc_extrapolate_kernel<<<(unsigned)ceil_div(rows * p, 256), 256, 0, s>>>(W, Wold, Z, R, B, rows, ld, p,
-                                                                              beta, gamma, first ? 1 : 0);
+void acc_extrapolate(cudaStream_t s, const float *W, float *Wold, float *Z, int64_t rows, int64_t ld, int p,
+                     float beta, bool first) {
+    acc_extrapolate_kernel<<<(unsigned)ceil_div(rows * p, 256), 256, 0, s>>>(W, Wold, Z, rows, ld, p, beta,
+                                                                              first ? 1 : 0);
     LRA_LAUNCHED();
 }
 

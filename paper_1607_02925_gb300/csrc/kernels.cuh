@@ -46,9 +46,11 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
 // M = lambda Wt - sum_c Gp[c] - B (dpad x p column-major); if norms: norms[0] =
 // ||M||_F^2, norms[1] = ||B||_F^2 (FP64).  If M == nullptr: G = sum_c Gp[c] is
 // written to G (dpad x p) instead.  scratch >= 2 * (dpad/32) doubles.
+// (Z != nullptr: M = lam Wt - G - (B + gamma Z) and norms[2] = ||(lam - gamma) Wt - G - B||^2;
+// scratch then holds 3 doubles per 16 rows)
 void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
-                     double *scratch);
+                     double *scratch, const float *Z = nullptr, double gamma = 0.0);
 
 // ---- anchor pass on tensor cores, BF16 X (k_anchor_tc.cu) ---------------
 // leading dimension of the hi/lo BF16 copy of Y (n rounded up to 64)
@@ -133,12 +135,8 @@ void col_dots(cudaStream_t s, const float *A, const float *B, int64_t rows, int6
 void scale_cols_rsqrt(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, const double *n2);
 // A = alpha * A (all rows x p)
 void scale_block(cudaStream_t s, float *A, int64_t rows, int64_t ld, int p, float alpha);
-// out[j] = sum_r (M - gamma (Wt - Z))[r, j]^2 (FP64), one block per column
-void acc_resid(cudaStream_t s, const float *M, const float *Wt, const float *Z, int64_t rows, int64_t ld,
-               int p, double gamma, double *out);
-// Z = W + beta (W - Wold), Wold = W, R = B + gamma Z; first: Z = W (Wold not read)
-void acc_extrapolate(cudaStream_t s, const float *W, float *Wold, float *Z, float *R, const float *B,
-                     int64_t rows, int64_t ld, int p, float beta, float gamma, bool first);
+void acc_extrapolate(cudaStream_t s, const float *W, float *Wold, float *Z, int64_t rows, int64_t ld, int p,
+                     float beta, bool first);
 
 // ---- sparse X (k_sparse.cu) -----------------------------------------------
 // Segment length of the row work list of X Y (rows longer than this are split).

@@ -131,6 +131,11 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
     // products and the final Rayleigh-Ritz step
     Workspace ws0(ctx, dpad, n, p + 1, nullptr, ws_items(mat));
     Engine e0(mat, ws0, s);
+    std::unique_ptr<KernelTimer> timer;
+    if (o.profile) {
+        timer.reset(new KernelTimer(s));
+        e0.timer = timer.get();
+    }
     e0.ensure_table(o.sampling);
     R.fro2 = mat->fro2;
     double delta = o.delta;
@@ -172,6 +177,7 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
         }
         Workspace ws(ctx, cur->dpad, cur->n, p, nullptr, ws_items(cur));
         Engine e(cur, ws, s);
+        e.timer = timer.get();
         e.ensure_table(o.sampling);
         int it3 = 0;
         lra_status st = e.alg3_a(kk, 1.0 / (9.0 * p * p), o.part_max_iters, seed_t, lam_hat.data(), it3);
@@ -256,6 +262,20 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
     R.x_passes += e0.stats.x_passes;
     R.status = status;
     R.kernel_launches = launches_of_thread() - launches0;
+    if (timer) {
+        double ms[KernelTimer::NKIND];
+        int64_t cnt[KernelTimer::NKIND], cols[KernelTimer::NKIND];
+        timer->collect(ms, cnt, cols);
+        for (int i = 0; i < KernelTimer::NKIND; ++i) R.phase_ms[i] = ms[i];
+        R.xtw_ms = ms[0];
+        R.xy_ms = ms[1];
+        R.inner_ms = ms[2];
+        R.xtw_launches = cnt[0];
+        R.xy_launches = cnt[1];
+        R.inner_launches = cnt[2];
+        R.xtw_cols = cols[0];
+        R.xy_cols = cols[1];
+    }
     R.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_all).count();
     if (rep) {
         const size_t sz = std::min(rep->struct_size ? rep->struct_size : sizeof(R), sizeof(R));
