@@ -236,6 +236,8 @@ lra_status lra_solve(lra_mat *mat, int k, int p, double eps, uint64_t seed, cons
  * is polled or cancelled. */
 lra_status lra_submit(lra_ctx *ctx, lra_mat *mat, int k, int p, double eps, uint64_t seed,
                       const lra_options *opt, lra_job *out);
+/* (options.partition = 1 gives LRA_EUNSUPPORTED here: its stages allocate
+ * deflated copies of X that a fixed admission footprint does not cover.) */
 
 /* Wait up to timeout_ms (0 = do not wait, < 0 = forever) for a job.  On
  * completion copies U/ritz/report (each may be NULL) as lra_solve would, frees

@@ -108,5 +108,9 @@ def test_partition_option_errors(ctx):
             o = lra.options(**bad)
             assert lra.lib.lra_solve(m, wl.k, wl.p, 1e-3, 0, ctypes.byref(o), Ud.data_ptr(), ritz.data_ptr(),
                                      None) == 1
+        # the request loop runs the q = k path only
+        job = ctypes.c_uint64()
+        o = lra.options(partition=1, delta=0.5)
+        assert lra.lib.lra_submit(ctx, m, wl.k, wl.p, 1e-3, 0, ctypes.byref(o), ctypes.byref(job)) == 11
     finally:
         lra.lra_mat_destroy(m)
