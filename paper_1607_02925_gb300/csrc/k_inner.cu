@@ -120,18 +120,24 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
                 for (int v = 0; v < 4; ++v) acc = fmaf(x[s][v], dl[s][v][j], acc);
             part[j] = warp_sum(acc);
         }
-        const int buf = (int)(t & 1);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
-        }
-        __syncthreads();
         float coef[PC];
+        if (nwarps == 1) {
+            // one warp: every lane already holds the full sum (no barrier)
 #pragma unroll
-        for (int j = 0; j < PC; ++j) {
-            float rj = 0.0f;
-            for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
-            coef[j] = eta * ci * rj;
+            for (int j = 0; j < PC; ++j) coef[j] = eta * ci * part[j];
+        } else {
+            const int buf = (int)(t & 1);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < PC; ++j) red[buf][warp][j] = part[j];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < PC; ++j) {
+                float rj = 0.0f;
+                for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
+                coef[j] = eta * ci * rj;
+            }
         }
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -359,10 +365,16 @@ template <typename TX>
 void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                     const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
                     int nb, float eta, float lam) {
-    // threads: 4 rows each, at most 512; S = row groups per thread
+    // threads: 4 rows each, at most 512; S = row groups per thread.  Up to
+    // d = 512 the one-sample step runs on a single warp (S <= 4): its x_i^T Delta
+    // is then reduced by shuffles alone, without a block barrier per step
     const int64_t groups = dpad / 4;
     int nt = (int)std::min<int64_t>(512, round_up(groups, 32));
     int64_t S = ceil_div(groups, nt);
+    if (nb == 1 && groups <= 128) {
+        nt = 32;
+        S = ceil_div(groups, 32);
+    }
     if (S > 8) {
         set_error("dense inner loop supports d <= 16384");
         throw Error{LRA_EUNSUPPORTED};
