@@ -33,6 +33,184 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// One sample per step on a single warp (d <= 512), two steps per iteration.
+// With Delta_{t+1} = a Delta_t + c_t x_t - eta M (a = 1 - eta lambda,
+// c_t = eta c_{i_t} r_t), the next step's r follows from dot products that do
+// not wait for c_t:
+//   r_{t+1} = a x_{t+1}^T Delta_t + c_t x_{t+1}^T x_t - x_{t+1}^T (eta M),
+// so the reduction for step t + 1 and the one for step t + 2 (taken on
+// Delta_{t+1} once c_t is known) run together, and the serial chain per step
+// is about half the dot-and-shuffle latency.  Lane l owns rows 4 (l + 32 s) + v.
+// The ring holds 8 columns, fetched 7 steps ahead.
+template <typename TX, int S, int PC>
+__global__ void __launch_bounds__(32) svrg_inner_pair_kernel(
+    const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
+    const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
+    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    constexpr int R = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [R][dpad]
+    const int lane = threadIdx.x;
+    const int j0 = blockIdx.x * PC;
+    constexpr int BYTES = 4 * sizeof(TX);
+
+    float dl[S][4][PC];   // Delta = W - Wt
+    float mm[S][4][PC];   // eta * M
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)lane + 32 * s);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            const bool ok = (r < dpad) && (j0 + j < p);
+            const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                dl[s][v][j] = ok ? (W[off + v] - Wt[off + v]) : 0.0f;
+                mm[s][v][j] = ok ? eta * M[off + v] : 0.0f;
+            }
+        }
+    }
+
+    auto prefetch = [&](int64_t t) {
+        if (t < m) {
+            const TX *col = X + (int64_t)idx[t] * ldx;
+            TX *slot = ring + (t & (R - 1)) * dpad;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int64_t r = 4 * ((int64_t)lane + 32 * s);
+                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+            }
+        }
+        cp_async_commit();
+    };
+    auto load = [&](int64_t t, float (&x)[S][4]) {
+        const TX *slot = ring + (t & (R - 1)) * dpad;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t r = 4 * ((int64_t)lane + 32 * s);
+            if (t < m && r < dpad) {
+                if constexpr (sizeof(TX) == 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
+                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
+                } else {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
+            }
+        }
+    };
+    // partial sums of y^T Delta, y^T (eta M) per column and y^T z
+    auto dots = [&](const float (&y)[S][4], const float (&z)[S][4], float (&u)[PC], float (&w)[PC], float &vv) {
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    a0 = fmaf(y[s][v], dl[s][v][j], a0);
+                    a1 = fmaf(y[s][v], mm[s][v][j], a1);
+                }
+            u[j] = a0;
+            w[j] = a1;
+        }
+        float a2 = 0.0f;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a2 = fmaf(y[s][v], z[s][v], a2);
+        vv = a2;
+    };
+    auto update = [&](const float (&x)[S][4], const float (&c)[PC], float a) {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int j = 0; j < PC; ++j) dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(c[j], x[s][v], -mm[s][v][j]));
+    };
+
+#pragma unroll
+    for (int u = 0; u < R - 1; ++u) prefetch(u);
+    const float a = 1.0f - eta * lam;
+    float x0[S][4], x1[S][4], x2[S][4];
+    float r[PC];
+    cp_async_wait<R - 2>();
+    load(0, x0);
+#pragma unroll
+    for (int j = 0; j < PC; ++j) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc = fmaf(x0[s][v], dl[s][v][j], acc);
+        r[j] = warp_sum(acc);
+    }
+    for (int64_t t = 0; t < m; t += 2) {
+        prefetch(t + R - 1);
+        prefetch(t + R);
+        cp_async_wait<R - 2>();
+        load(t + 1, x1);
+        load(t + 2, x2);
+        const float c0 = eta * cval[t];
+        const float c1v = (t + 1 < m) ? eta * cval[t + 1] : 0.0f;
+        float ct[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
+        // chain A: r_{t+1} from Delta_t
+        float uA[PC], wA[PC], vA;
+        dots(x1, x0, uA, wA, vA);
+        // step t
+        update(x0, ct, a);
+        // chain B: r_{t+2} from Delta_{t+1}, less the c_{t+1} term
+        float uB[PC], wB[PC], vB;
+        dots(x2, x1, uB, wB, vB);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            uA[j] = warp_sum(uA[j]);
+            wA[j] = warp_sum(wA[j]);
+            uB[j] = warp_sum(uB[j]);
+            wB[j] = warp_sum(wB[j]);
+        }
+        vA = warp_sum(vA);
+        vB = warp_sum(vB);
+        float c1[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            const float r1 = fmaf(a, uA[j], fmaf(ct[j], vA, -wA[j]));
+            c1[j] = c1v * r1;
+        }
+        if (t + 1 < m) {
+            // step t + 1
+            update(x1, c1, a);
+#pragma unroll
+            for (int j = 0; j < PC; ++j) r[j] = fmaf(a, uB[j], fmaf(c1[j], vB, -wB[j]));
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x0[s][v] = x2[s][v];
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r0 = 4 * ((int64_t)lane + 32 * s);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            if (r0 < dpad && j0 + j < p) {
+                const int64_t off = r0 + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) W[off + v] = Wt[off + v] + dl[s][v][j];
+            }
+        }
+    }
+}
+
 // One sample per step.  Thread t owns rows 4 (t + s NT) + v for s < S, v < 4
 // (rows >= dpad skipped).
 template <typename TX, int S, int PC>
@@ -361,6 +539,16 @@ constexpr size_t dt_size() { return sizeof(TX); }
 
 constexpr size_t kRingBytes = 220 * 1024;
 
+template <typename TX, int S, int PC>
+void launch_pair(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W, const float *Wt,
+                 const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam) {
+    auto k = svrg_inner_pair_kernel<TX, S, PC>;
+    const size_t smem = (size_t)8 * dpad * sizeof(TX);
+    ensure_smem(k, (int)smem);
+    k<<<(unsigned)ceil_div(p, PC), 32, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    LRA_LAUNCHED();
+}
+
 template <typename TX>
 void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                     const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
@@ -386,6 +574,23 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
         if ((size_t)kRing * dpad * (dt_size<TX>()) > kRingBytes) {
             set_error("dense inner loop: d too large for the shared-memory ring");
             throw Error{LRA_EUNSUPPORTED};
+        }
+        if (nt == 32) {
+            // a single warp: two steps per iteration with the look-ahead identity
+#define LRA_PAIR_CASE(SS, PCC)                                                                          \
+    if (S == SS && pc == PCC) {                                                                         \
+        launch_pair<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);               \
+        return;                                                                                         \
+    }
+            LRA_PAIR_CASE(1, 1)
+            LRA_PAIR_CASE(1, 2)
+            LRA_PAIR_CASE(2, 1)
+            LRA_PAIR_CASE(2, 2)
+            LRA_PAIR_CASE(3, 1)
+            LRA_PAIR_CASE(3, 2)
+            LRA_PAIR_CASE(4, 1)
+            LRA_PAIR_CASE(4, 2)
+#undef LRA_PAIR_CASE
         }
 #define LRA_INNER_CASE(SS, PCC)                                                                     \
     if (S == SS && pc == PCC) {                                                                     \
