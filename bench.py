@@ -523,6 +523,9 @@ def run_lra(args):
                 if steps > 0:
                     e["steps"] = steps
                     e["ns_per_step"] = tot[kk] * 1e6 / steps
+                    # every CTA of the one-sample loop owns a column group on its
+                    # own SM and takes all m steps: steps/s per SM = 1 / step time
+                    e["steps_per_s_per_sm"] = 1e9 / e["ns_per_step"]
             per_kernel[kk] = e
 
     # end to end through the C ABI with host buffers
