@@ -14,7 +14,8 @@ from ._ffi import (LRA_BF16, LRA_F16, LRA_F32, LRA_F64, LRA_MAX_P, LRA_NOALLOC_M
                    LRA_SAMPLE_IMPORTANCE,
                    LRA_SAMPLE_UNIFORM, LRA_SHIFT_FAR, LRA_SHIFT_FIXED, LRA_SHIFT_PAPER,
                    LRA_STREAM_DELTA, LRA_STREAM_INIT, LRA_STREAM_POWER_A, LRA_STREAM_POWER_D,
-                   LRA_STREAM_SVRG, STATUS, LraError, LraOptions, LraReport, LraSolveInfo,
+                   LRA_STREAM_BLOCK, LRA_STREAM_PART, LRA_STREAM_SVRG, STATUS, LraError, LraOptions,
+                   LraReport, LraSolveInfo,
                    declared_symbols, lib, library_path)
 
 __all__ = [n for n in dir() if n.startswith(("LRA_", "Lra", "lra_"))] + [

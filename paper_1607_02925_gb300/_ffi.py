@@ -18,6 +18,7 @@ LRA_F32, LRA_BF16, LRA_F16, LRA_F64 = 0, 1, 2, 3
 LRA_SHIFT_PAPER, LRA_SHIFT_FAR, LRA_SHIFT_FIXED = 0, 1, 2
 LRA_SAMPLE_IMPORTANCE, LRA_SAMPLE_UNIFORM = 0, 1
 LRA_STREAM_INIT, LRA_STREAM_POWER_A, LRA_STREAM_POWER_D, LRA_STREAM_SVRG, LRA_STREAM_DELTA = 1, 2, 3, 4, 5
+LRA_STREAM_PART, LRA_STREAM_BLOCK = 6, 7
 LRA_MAX_P = 112
 LRA_NOALLOC_MAX_N = 1 << 24
 STATUS = ["LRA_OK", "LRA_EINVAL", "LRA_ENOMEM", "LRA_ECUDA", "LRA_ENOTCONV", "LRA_EDIVERGED",

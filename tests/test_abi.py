@@ -37,6 +37,15 @@ def test_options_defaults_and_status_names(lra):
     assert (o.shift_policy, o.theta_eta, o.theta_m, o.max_epochs, o.max_outer) == (0, 0.25, 2.0, 60, 2000)
     assert lra.lra_status_str(0) == "LRA_OK"
     assert lra.lra_status_str(11) == "LRA_EUNSUPPORTED"
+    # the accelerated and partitioned options default off, with the oracle's parameters
+    from oracle import lra_oracle as O
+    from oracle import lra_partition as P
+    oo = O.Options()
+    assert (o.acc, o.acc_theta, o.acc_max_outer, o.acc_target) == (0, oo.acc_theta, oo.acc_max_outer,
+                                                                    oo.acc_target)
+    assert (o.partition, o.part_max_iters) == (0, 2000)
+    assert P.adaptive_solve.__defaults__[-1] == o.part_max_iters
+    assert (lra.LRA_STREAM_PART, lra.LRA_STREAM_BLOCK) == (P.STREAM_PART, P.STREAM_BLOCK)
 
 
 def test_struct_layouts_match_header(lra):
