@@ -144,13 +144,15 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
         if (st != LRA_OK) return st;
     }
     R.delta = delta;
-    float *Ucols = static_cast<float *>(dev_alloc(ctx, sizeof(float) * dpad * p));
-    struct Free {
+    struct Buf {  // device buffer released on every exit path
         lra_ctx *c;
-        void *p;
         size_t b;
-        ~Free() { dev_free(c, p, b); }
-    } free_u{ctx, Ucols, sizeof(float) * dpad * p};
+        void *p;
+        Buf(lra_ctx *c_, size_t b_) : c(c_), b(b_), p(dev_alloc(c_, b_)) {}
+        ~Buf() { dev_free(c, p, b); }
+    };
+    Buf ubuf(ctx, sizeof(float) * dpad * p);
+    float *Ucols = static_cast<float *>(ubuf.p);
     LRA_CUDA(cudaMemsetAsync(Ucols, 0, sizeof(float) * dpad * p, s));
 
     lra_status status = LRA_OK;
@@ -166,12 +168,14 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
             // X_{-(s-1)} = X - U (X^T U)^T, then a matrix of the original storage
             const int PP = pad_p(ncols);
             e0.xt_mul(Ucols, ncols, ws0.Y, false);
-            float *tmp = static_cast<float *>(dev_alloc(ctx, sizeof(float) * dpad * n));
-            deflate(s, mat, Ucols, ncols, ws0.Y, PP, tmp);
-            LRA_CUDA(cudaStreamSynchronize(s));
-            const lra_dtype storage = mat->sp ? LRA_F32 : mat->storage;
-            const lra_status st = lra_create_dense(ctx, d, n, LRA_F32, tmp, dpad, 1, storage, &defl.m);
-            dev_free(ctx, tmp, sizeof(float) * dpad * n);
+            lra_status st;
+            {
+                Buf tmp(ctx, sizeof(float) * dpad * n);
+                deflate(s, mat, Ucols, ncols, ws0.Y, PP, static_cast<float *>(tmp.p));
+                LRA_CUDA(cudaStreamSynchronize(s));
+                const lra_dtype storage = mat->sp ? LRA_F32 : mat->storage;
+                st = lra_create_dense(ctx, d, n, LRA_F32, tmp.p, dpad, 1, storage, &defl.m);
+            }
             if (st != LRA_OK) return st;
             cur = defl.m;
         }
