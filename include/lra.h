@@ -52,7 +52,7 @@ typedef enum {
     LRA_EAGAIN = 8,       /* lra_poll with timeout 0: job still queued or running */
     LRA_EBUSY = 9,        /* the object is in use by a running job */
     LRA_ECANCELLED = 10,  /* the job was cancelled */
-    LRA_EUNSUPPORTED = 11 /* valid request this build does not implement (e.g. p > 112) */
+    LRA_EUNSUPPORTED = 11 /* valid request the library does not implement (e.g. p > 112) */
 } lra_status;
 
 typedef enum { LRA_F32 = 0, LRA_BF16 = 1, LRA_F16 = 2, LRA_F64 = 3 } lra_dtype;

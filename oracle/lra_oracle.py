@@ -20,7 +20,7 @@ Everything is plain FP64 numpy (library primitives: matmul, QR, eigh,
 searchsorted) except the SVRG inner loop, which is the plain C in svrg_inner.c.
 X is read exactly as stored (FP64 or FP32 values widened).
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
   * SVRGsolve's update is not printed; the step used is the variance-reduced
     gradient of the quadratic F(W) = 1/2 tr W^T(lambda I - A)W - tr B^T W with
     importance sampling q_i ~ ||x_i||^2 and c_i = 1/q_i (svrg_epoch).

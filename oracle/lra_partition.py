@@ -21,7 +21,7 @@ Sec. 3 assumes ("we already applied the projection ... to the columns of X"):
 The columns are then orthonormalised together and Algorithm 2 with X X^T
 returns U.
 
-Readings (each also listed in the design doc):
+Readings:
   * D_{-(s-1)} = P (lambda I - A)^{-1} P (Eq. deflatedShift) is taken as
     P (lambda I - A_{-(s-1)})^{-1} P: the same operator when the u_i are exact
     eigenvectors, and the one SVRG can solve (lambda I - A is indefinite for

@@ -4,7 +4,7 @@ All inputs are seeded and synthetic (lra_inputs, or a test-local numpy
 generator for arbitrary step inputs); every expected value comes from
 oracle/.  Tolerances:
   * integer / index work (sampling weights, prefix sums, sampled indices): exact;
-  * FP32 arithmetic over sums of N terms: relative 1e-5 (spec bound for the
+  * FP32 arithmetic over sums of N terms: relative 1e-5 (the stated accuracy of the
     FP32 path; the observed error is ~1e-6);
   * subspaces: sin of the largest principal angle <= 1e-4 (FP32 X), 1e-3 (BF16 X).
 """
