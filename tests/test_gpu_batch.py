@@ -153,3 +153,28 @@ def test_batch_errors(ctx):
         assert lra.lib.lra_solve(m, 3, 6, 1e-3, 0, ctypes.byref(o), U.data_ptr(), r.data_ptr(), None) == 11
     finally:
         lra.lra_mat_destroy(m)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_non_finite_dense_input_returns_a_status(ctx, bad):
+    """A NaN or Inf entry in a dense X ends the solve with a status (divergence at
+    the first anchor, a failed Cholesky, or no sampleable column), and the
+    context still solves the next matrix."""
+    d, n = 256, 800
+    Xt = planted(d, n, 3, 5)
+    Xbad = Xt.copy()
+    Xbad[17, 40] = bad
+    U = torch.zeros(3, d, device=DEV)
+    r = torch.zeros(3, dtype=torch.float64, device=DEV)
+    o = lra.options(shift_policy=lra.LRA_SHIFT_FAR)
+    m = lra.lra_create_dense(ctx, d, n, lra.LRA_F32, Xbad, d, False, lra.LRA_F32)
+    try:
+        st = lra.lib.lra_solve(m, 3, 6, 1e-3, 0, ctypes.byref(o), U.data_ptr(), r.data_ptr(), None)
+        assert st in (1, 5, 6)
+    finally:
+        lra.lra_mat_destroy(m)
+    m = lra.lra_create_dense(ctx, d, n, lra.LRA_F32, Xt, d, False, lra.LRA_F32)
+    try:
+        assert lra.lib.lra_solve(m, 3, 6, 1e-3, 0, ctypes.byref(o), U.data_ptr(), r.data_ptr(), None) == 0
+    finally:
+        lra.lra_mat_destroy(m)
