@@ -55,3 +55,15 @@ def test_replicas_take_the_max_step_time_over_ranks():
     assert [o[0] for o in out] == [0, 1]
     assert all(o[1] == world and o[2] == o[0] for o in out)
     assert all(o[3] == 17.5 for o in out)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    """Under torchrun the reference arm (the oracle on the host cores) is timed
+    and printed by rank 0; every other rank exits 0 without work."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.dist_env() == (1, 2, 1)
+    assert bench.run_reference(None) == 0
