@@ -27,10 +27,7 @@ import paper_1607_02925_gb300 as lra  # noqa: E402
 DEV = "cuda"
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+from measures import elem_bound, elem_rms, rel  # noqa: E402,F401
 
 
 def cm(t):
@@ -80,6 +77,7 @@ def test_fixed_schedule_matches_oracle(ctx, p, batch):
         assert info.gamma == pytest.approx(g, rel=1e-12)
         assert info.inner_steps == sto.inner_steps and info.epochs == sto.epochs
         assert rel(cm(W), Wo) < 2e-5
+        assert elem_rms(cm(W), Wo) < 2e-5
         assert info.residual == pytest.approx(sto.residual, rel=1e-3)
     finally:
         lra.lra_mat_destroy(m)
@@ -142,6 +140,7 @@ def test_sparse_fixed_schedule_matches_oracle(ctx):
         Wo, sto = ctxo.acc_svrg_solve(B.astype(np.float64), np.zeros((d, p)), lam, mu, lam1)
         assert st == 0 and info.outer == 3 and info.inner_steps == sto.inner_steps
         assert rel(cm(W), Wo) < 2e-5
+        assert elem_rms(cm(W), Wo) < 2e-5
     finally:
         lra.lra_mat_destroy(m)
 

@@ -22,10 +22,7 @@ import paper_1607_02925_gb300 as lra  # noqa: E402
 DEV = "cuda"
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+from measures import elem_bound, elem_rms, rel  # noqa: E402,F401
 
 
 def cm(t):
@@ -78,6 +75,7 @@ def test_dense_batched_inner_matches_oracle(ctx, d, n, p, batch, storage):
         ref = O.svrg_epoch(Xo, W0.astype(np.float64), Wt.astype(np.float64), M.astype(np.float64), idx,
                            c.astype(np.float64), eta, lam, batch=batch)
         assert rel(cm(W) - Wt, ref - Wt) < 1e-5
+        assert elem_rms(cm(W) - Wt, ref - Wt) < 1e-5
     finally:
         lra.lra_mat_destroy(m)
 
@@ -106,6 +104,7 @@ def test_sparse_batched_inner_matches_oracle(ctx, batch, steps):
         ref = O.svrg_epoch(Xs, W0.astype(np.float64), Wt.astype(np.float64), M.astype(np.float64), idx,
                            c.astype(np.float64), eta, lam, batch=batch)
         assert rel(cm(W) - Wt, ref - Wt) < 1e-5
+        assert elem_rms(cm(W) - Wt, ref - Wt) < 1e-5
     finally:
         lra.lra_mat_destroy(m)
 

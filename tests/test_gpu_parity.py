@@ -27,10 +27,7 @@ import paper_1607_02925_gb300 as lra  # noqa: E402
 DEV = "cuda"
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+from measures import elem_bound, elem_rms, rel  # noqa: E402
 
 
 def cm(t):
@@ -157,19 +154,27 @@ def test_anchor_matches_oracle(ctx, d, n, p, storage):
     try:
         M = torch.zeros(p, d, dtype=torch.float32, device=DEV)
         nM2, nB2 = lra.lra_anchor(m.h, p, dev_block(Wt), dev_block(B), lam, M)
-        ref = O.anchor(Xt, Wt.astype(np.float64), B.astype(np.float64), lam)
+        W64, B64 = Wt.astype(np.float64), B.astype(np.float64)
+        ref = O.anchor(Xt, W64, B64, lam)
+        aX = np.abs(np.asarray(Xt, dtype=np.float64))          # n x d = |X|^T
+        sY = aX @ np.abs(W64)                                    # |X|^T |W|
+        sM = lam * np.abs(W64) + aX.T @ sY + np.abs(B64)         # |lam W| + |X| |X|^T |W| + |B|
         assert rel(cm(M), ref) < 1e-5
+        assert elem_bound(cm(M), ref, sM) < 1e-5
         assert abs(nM2 / np.sum(ref ** 2) - 1) < 1e-5
-        assert abs(nB2 / np.sum(B.astype(np.float64) ** 2) - 1) < 1e-12
+        assert abs(nB2 / np.sum(B64 ** 2) - 1) < 1e-12
         # the two passes separately
         Y = torch.zeros(p, n, dtype=torch.float32, device=DEV)
         lra.lra_xt_mul(m.h, p, dev_block(Wt), Y)
-        Yref = np.asarray(Xt, dtype=np.float64) @ Wt.astype(np.float64)
-        assert rel(Y.double().cpu().numpy().T, Yref) < 1e-5
+        Yref = np.asarray(Xt, dtype=np.float64) @ W64
+        Yg = Y.double().cpu().numpy().T
+        assert rel(Yg, Yref) < 1e-5
+        assert elem_bound(Yg, Yref, sY) < 1e-5
         G = torch.zeros(p, d, dtype=torch.float32, device=DEV)
         lra.lra_x_mul(m.h, p, Y, G)
-        Gref = np.asarray(Xt, dtype=np.float64).T @ Y.double().cpu().numpy().T
+        Gref = np.asarray(Xt, dtype=np.float64).T @ Yg
         assert rel(cm(G), Gref) < 1e-5
+        assert elem_bound(cm(G), Gref, aX.T @ np.abs(Yg)) < 1e-5
     finally:
         m.close()
 
@@ -197,6 +202,7 @@ def test_inner_loop_matches_oracle(ctx, d, n, p):
         ref = O.svrg_epoch(Xt, W0.astype(np.float64), Wt.astype(np.float64), M.astype(np.float64),
                            idx.astype(np.int64), c.astype(np.float64), eta, lam)
         assert rel(cm(W) - Wt, ref - Wt) < 1e-5
+        assert elem_rms(cm(W) - Wt, ref - Wt) < 1e-5
         # m = 0 leaves W unchanged
         W = dev_block(W0)
         lra.lra_svrg_inner(m.h, p, W, dev_block(Wt), dev_block(M), None, 0, None, eta, lam)
@@ -231,6 +237,7 @@ def test_svrg_solve_matches_oracle_and_dense_solve(ctx):
         assert info.m == math.ceil(2.0 / (0.25 * mu / (lam ** 2 + ctxo.table.kappa * lam1_up) * mu))
         assert info.epochs == sto.epochs
         assert rel(cm(W), Wo) < 2e-5
+        assert elem_rms(cm(W), Wo) < 2e-5
     finally:
         m.close()
 
@@ -246,13 +253,17 @@ def test_gram_and_cholqr2(ctx, rows, p):
     A = A.astype(np.float32)
     G = torch.zeros(p, p, dtype=torch.float64, device=DEV)
     lra.lra_gram(ctx, rows, p, dev_block(A), rows, G)
-    Gref = A.astype(np.float64).T @ A.astype(np.float64)
+    A64 = A.astype(np.float64)
+    Gref = A64.T @ A64
     assert rel(G.cpu().numpy().T, Gref) < 1e-6
+    assert elem_bound(G.cpu().numpy().T, Gref, np.abs(A64).T @ np.abs(A64)) < 1e-6
     W = dev_block(A)
     lra.lra_cholqr2(ctx, rows, p, W)
     Q = cm(W)
     assert np.max(np.abs(Q.T @ Q - np.eye(p))) < 2e-6
-    assert rel(Q, O.orth(A.astype(np.float64))) < 1e-5
+    Qref = O.orth(A64)
+    assert rel(Q, Qref) < 1e-5
+    assert elem_rms(Q, Qref) < 1e-5
 
 
 def test_cholqr2_reports_rank_deficiency(ctx):
@@ -299,6 +310,8 @@ def test_rayleigh_ritz(ctx, storage):
             Xref = Xt if (use32 or storage == lra.LRA_F32) else X_st
             rho, Uh, Q, Href = O.rayleigh_ritz(Xref, S.astype(np.float32).astype(np.float64))
             assert rel(H.cpu().numpy().T, Href) < 1e-5
+            aQ = np.abs(np.asarray(Xref, dtype=np.float64)) @ np.abs(S)
+            assert elem_bound(H.cpu().numpy().T, Href, aQ.T @ aQ) < 1e-5
             assert np.max(np.abs(ev.cpu().numpy() - rho)) < 1e-5 * rho[0]
     finally:
         m.close()
@@ -343,6 +356,47 @@ def test_shift_tuning_matches_oracle(ctx):
         assert res["solve_count"] == octx.solve_count
     finally:
         m.close()
+
+
+def test_delta_estimate_matches_oracle(ctx):
+    """Sec. 3's gap budget (no procedure printed; Algorithm 3 on A with p + 1
+    vectors, eps' = 1/(9 p^2)): the GPU estimate equals the oracle's and lies in
+    Theorem 4's interval around (lambda_k - lambda_{p+1}) / 1.5."""
+    for d, n, k, p, seed, sig in [(48, 384, 5, 10, 11, L.sigma_small_gap(48)),
+                                  (256, 2048, 5, 10, 0, L.sigma_small_gap(256)),
+                                  (300, 3001, 20, 40, 3, L.sigma_steep_head(300))]:
+        Xt, U, s = L.planted_numpy(d, n, sig, seed + 100)
+        Xt = np.ascontiguousarray(Xt.astype(np.float32))
+        m = Mat(ctx, Xt)
+        try:
+            dg = lra.lra_delta_estimate(m.h, k, p, seed)
+        finally:
+            m.close()
+        do = O.delta_estimate(O.Context(Xt, seed, O.Options()), k, p)
+        # each Ritz value within 1e-5 of rho_1 (the FP32 tolerance of the Ritz
+        # step), so their difference over 1.5 within 2e-5 rho_1 / 1.5
+        assert abs(dg - do) <= 2e-5 * s[0] ** 2 / 1.5, (d, dg, do)
+        lam = s ** 2
+        eps = 1.0 / (9.0 * p * p)
+        assert ((1 - eps) * lam[k - 1] - lam[p]) / 1.5 * (1 - 1e-5) <= dg <= (lam[k - 1] - (1 - eps) * lam[p]) / 1.5 * (1 + 1e-5)
+
+
+def test_solve_paper_shift_with_estimated_delta(ctx):
+    """lra_solve under the PAPER policy with delta = 0 estimates the gap budget
+    itself: the same Delta, shift and number of Algorithm 7 rounds as the
+    oracle's run, and the returned U meets ratio <= 1 + eps."""
+    sig = L.sigma_small_gap(48)
+    Xt64, U, s = L.planted_numpy(48, 384, sig, 7)
+    Xt = np.ascontiguousarray(Xt64.astype(np.float32))
+    k, p = 5, 10
+    st, Ug, rg, rep = run_solve(ctx, Xt, k, p, 11, src=Xt64, shift_policy=lra.LRA_SHIFT_PAPER, delta=0.0)
+    assert st == 0
+    ref = O.solve(Xt, k, p, 1e-3, 11, O.Options(shift_policy=O.SHIFT_PAPER, delta=0.0))
+    assert abs(rep.delta / ref.delta - 1) < 1e-5
+    assert rep.shift_rounds == ref.shift.rounds
+    assert abs(rep.lambda_ / ref.lam - 1) < 1e-5
+    ratio = O.frobenius_error(Xt64, Ug) / L.closed_form_opt(s, k)
+    assert 1.0 - 1e-6 <= ratio <= 1.0 + 1e-3
 
 
 # ---------------------------------------------------------------------------

@@ -26,10 +26,7 @@ import paper_1607_02925_gb300 as lra  # noqa: E402
 DEV = "cuda"
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+from measures import elem_bound, elem_rms, rel  # noqa: E402,F401
 
 
 def cm(t):
@@ -117,17 +114,25 @@ def test_anchor_and_products_match_oracle(ctx, d, n, p):
         lam = 1.7
         M = torch.zeros(p, d, dtype=torch.float32, device=DEV)
         nM2, nB2 = lra.lra_anchor(m.h, p, dev_block(Wt), dev_block(B), lam, M)
-        ref = O.anchor(m.Xt, Wt.astype(np.float64), B.astype(np.float64), lam)
+        W64, B64 = Wt.astype(np.float64), B.astype(np.float64)
+        ref = O.anchor(m.Xt, W64, B64, lam)
+        aX = abs(O.as64(m.Xt))                                   # |X|^T, sparse
+        sY = np.asarray(aX @ np.abs(W64))
+        sM = lam * np.abs(W64) + np.asarray(aX.T @ sY) + np.abs(B64)
         assert rel(cm(M), ref) < 1e-5
+        assert elem_bound(cm(M), ref, sM) < 1e-5
         assert abs(nM2 / np.sum(ref ** 2) - 1) < 1e-5
         Y = torch.zeros(p, n, dtype=torch.float32, device=DEV)
         lra.lra_xt_mul(m.h, p, dev_block(Wt), Y)
-        Yref = np.asarray(O.as64(m.Xt) @ Wt.astype(np.float64))
-        assert rel(Y.double().cpu().numpy().T, Yref) < 1e-5
+        Yref = np.asarray(O.as64(m.Xt) @ W64)
+        Yg = Y.double().cpu().numpy().T
+        assert rel(Yg, Yref) < 1e-5
+        assert elem_bound(Yg, Yref, sY) < 1e-5
         G = torch.zeros(p, d, dtype=torch.float32, device=DEV)
         lra.lra_x_mul(m.h, p, Y, G)
-        Gref = np.asarray(O.as64(m.Xt).T @ Y.double().cpu().numpy().T)
+        Gref = np.asarray(O.as64(m.Xt).T @ Yg)
         assert rel(cm(G), Gref) < 1e-5
+        assert elem_bound(cm(G), Gref, np.asarray(aX.T @ np.abs(Yg))) < 1e-5
     finally:
         m.close()
 
@@ -156,6 +161,7 @@ def test_inner_loop_matches_oracle(ctx, d, n, p, steps):
         ref = O.svrg_epoch(m.Xt, W0.astype(np.float64), Wt.astype(np.float64), M.astype(np.float64),
                            idx, c.astype(np.float64), eta, lam)
         assert rel(cm(W) - Wt, ref - Wt) < 1e-5
+        assert elem_rms(cm(W) - Wt, ref - Wt) < 1e-5
     finally:
         m.close()
 

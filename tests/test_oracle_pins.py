@@ -320,6 +320,41 @@ def test_shift_tuning_invariants(small_planted):
     assert 0 < sh.mu_lb <= sh.lam - lam1
 
 
+
+def _slow_tail_planted():
+    """lambda = 10, 9, 8 | 5, 4.9, 4.8 | 4.0, then 89 eigenvalues just below
+    0.97 * 4.0: with k = 3, p = 6 the (p+1)-th Ritz value converges at the slow
+    ratio ~0.97 per power step against a heavy tail, so Theorem 4's accuracy
+    eps' = 1/(9 p^2) is reached only after many steps (20 are too few)."""
+    lam = np.array([10.0, 9.0, 8.0, 5.0, 4.9, 4.8, 4.0] + [4.0 * 0.97 * (1 - 0.001 * j) for j in range(89)])
+    Xt, U, s = L.planted_numpy(96, 600, np.sqrt(lam), 21)
+    return Xt, s
+
+
+def _check_delta_estimate(delta_fn):
+    """Sec. 3's gap budget: Delta <= lambda_k - lambda_{p+1} <= 2 Delta.  The
+    estimate is (rho_k - rho_{p+1}) / 1.5 with rho from Algorithm 3 at
+    eps' = 1/(9 p^2); Theorem 4 gives (1 - eps') lambda_i <= rho_i and
+    Rayleigh-Ritz values never exceed the eigenvalues (Cauchy interlacing), so
+    the estimate lies in [((1-eps') l_k - l_{p+1}) / 1.5, (l_k - (1-eps') l_{p+1}) / 1.5]."""
+    cases = [(L.planted_numpy(48, 384, L.sigma_small_gap(48), 7)[0], L.sigma_small_gap(48), 5, 10, 11)]
+    Xs, ss = _slow_tail_planted()
+    cases.append((Xs, ss, 3, 6, 4))
+    for Xt, s, k, p, seed in cases:
+        lam = np.asarray(s, dtype=np.float64) ** 2
+        eps = 1.0 / (9.0 * p * p)
+        lk, lp1 = lam[k - 1], lam[p]
+        dh = delta_fn(O.Context(Xt, seed, O.Options()), k, p)
+        lo = ((1.0 - eps) * lk - lp1) / 1.5
+        hi = (lk - (1.0 - eps) * lp1) / 1.5
+        assert lo * (1 - 1e-12) <= dh <= hi * (1 + 1e-12), (k, p, dh, lo, hi)
+        assert dh <= lk - lp1 <= 2.0 * dh
+
+
+def test_delta_estimate_theorem4_interval():
+    _check_delta_estimate(O.delta_estimate)
+
+
 def test_subspace_iteration_rate_matches_theory(small_planted):
     """Algorithm 1 on D = (lambda I - A)^{-1}: the top-k directions converge at
     the ratio of D's eigenvalues, (lambda - lambda_j)/(lambda - lambda_{p+1}) for
@@ -423,3 +458,23 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(O, "svrg_epoch", bad_epoch)
     assert _pin_raises(test_inner_step_is_unbiased_gradient_step)
     monkeypatch.setattr(O, "svrg_epoch", real_epoch)
+
+
+    # gap budget: rho_p in place of rho_{p+1}, a second division by 1.5, and
+    # too few power steps (L = 20) each leave Theorem 4's interval
+    def delta_variant(rho_index_shift=0, div=1.5, steps=None):
+        def fn(ctx, k, p):
+            d = ctx.d
+            eps = 1.0 / (9.0 * p * p)
+            Lsteps = steps or min(200, int(math.ceil((1.0 / eps) * math.log(d / eps))))
+            S = O.orth(O.gaussian_block(ctx.seed, O.STREAM_DELTA, 0, d, p + 1))
+            for _ in range(Lsteps):
+                S = O.orth(O.x_apply(ctx.Xt, S))
+            rho = O.rayleigh_ritz(ctx.Xt, S)[0]
+            return float(rho[k - 1] - rho[p - rho_index_shift]) / div
+        return fn
+
+    _check_delta_estimate(delta_variant())          # the restatement itself passes
+    assert _pin_raises(lambda: _check_delta_estimate(delta_variant(rho_index_shift=1)))
+    assert _pin_raises(lambda: _check_delta_estimate(delta_variant(div=1.5 * 1.5)))
+    assert _pin_raises(lambda: _check_delta_estimate(delta_variant(steps=20)))
