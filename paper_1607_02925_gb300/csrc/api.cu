@@ -1,6 +1,7 @@
 // C ABI entry points (include/lra.h): argument validation, object lifetime,
 // conversion between the caller's layouts (leading dimension d) and the
 // library's padded device layouts, and error-status translation.
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -520,10 +521,15 @@ lra_status lra_sampling_table(lra_ctx *ctx, int64_t n, const double *norm2, int 
             sum_max(s, norm2, n, sm, nullptr);
             sampling_table(s, norm2, n, mode, sm + 1, cum, c, sm + 2, static_cast<uint64_t *>(scr));
             uint64_t tot = 0;
-            double kp = 0;
+            double kp = 0, sum = 0;
             LRA_CUDA(cudaMemcpyAsync(&tot, cum + n - 1, sizeof(tot), cudaMemcpyDeviceToHost, s));
             LRA_CUDA(cudaMemcpyAsync(&kp, sm + 2, sizeof(kp), cudaMemcpyDeviceToHost, s));
+            LRA_CUDA(cudaMemcpyAsync(&sum, sm, sizeof(sum), cudaMemcpyDeviceToHost, s));
             LRA_CUDA(cudaStreamSynchronize(s));
+            if (!std::isfinite(sum)) {
+                dev_free(ctx, scr, scr_bytes);
+                return einval("a column norm is not finite");
+            }
             if (total) *total = tot;
             if (kappa) *kappa = kp;
         } catch (...) {

@@ -267,6 +267,10 @@ void Engine::ensure_norms() {
     double h[2];
     LRA_CUDA(cudaMemcpyAsync(h, mat_->dev_sm, sizeof(h), cudaMemcpyDeviceToHost, s_));
     sync();
+    if (!std::isfinite(h[0])) {
+        set_error("X has a non-finite entry (||X||_F^2 is not finite)");
+        throw Error{LRA_EINVAL};
+    }
     mat_->fro2 = h[0];
     mat_->maxn = h[1];
     mat_->have_norms = true;

@@ -11,10 +11,13 @@
 // The scratch array lives for as long as the library is loaded, on every GPU
 // that loads it.  All calls share it: two calls whose work overlaps on the GPU
 // (different streams or threads) race on it and must be serialised by the
-// caller.  The first call on a device looks up the array's device address with
-// that device current; make that first call before any stream capture.
+// caller.  The first call on a device (and the first after a device reset,
+// which gives the device a new context) looks up the array's device address
+// with that device current; make that first call before any stream capture.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "engine.h"
@@ -29,26 +32,61 @@ constexpr int64_t kScratchWords = LRA_NOALLOC_MAX_N / 256 + 64;
 __device__ __align__(256) uint64_t g_table_scratch[kScratchWords];
 
 std::mutex g_addr_mu;
-void *g_addr[64] = {nullptr};
 
-// Device address of g_table_scratch on the current device (looked up once).
+// The address is cached per device together with the CUDA context it was
+// looked up in: after a device reset the primary context, and with it the
+// array's address, is new, so a changed context triggers a fresh lookup.
+struct CachedAddr {
+    CUcontext ctx = nullptr;
+    void *ptr = nullptr;
+};
+CachedAddr g_addr[64];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+
+CUcontext current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            cudaGetLastError();
+            set_error("cuCtxGetCurrent not available");
+            throw Error{LRA_ECUDA};
+        }
+        fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    }
+    CUcontext c = nullptr;
+    if (fn(&c) != CUDA_SUCCESS) {
+        set_error("cuCtxGetCurrent failed");
+        throw Error{LRA_ECUDA};
+    }
+    return c;
+}
+
+// Device address of g_table_scratch on the current device, looked up with
+// cudaGetSymbolAddress on the first call in each CUDA context.
 uint64_t *scratch_address(int device) {
     std::lock_guard<std::mutex> g(g_addr_mu);
     if (device < 0 || device >= 64) {
         set_error("device index out of range for the fixed scratch table");
         throw Error{LRA_EUNSUPPORTED};
     }
-    if (!g_addr[device]) {
+    const CUcontext cur = current_context();
+    CachedAddr &e = g_addr[device];
+    if (!e.ptr || e.ctx != cur) {
         void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_table_scratch);
-        if (e != cudaSuccess || !ptr) {
+        const cudaError_t st = cudaGetSymbolAddress(&ptr, g_table_scratch);
+        if (st != cudaSuccess || !ptr) {
             cudaGetLastError();
-            set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(st));
             throw Error{LRA_ECUDA};
         }
-        g_addr[device] = ptr;
+        e.ptr = ptr;
+        e.ctx = current_context();
     }
-    return static_cast<uint64_t *>(g_addr[device]);
+    return static_cast<uint64_t *>(e.ptr);
 }
 
 }  // namespace
@@ -85,16 +123,22 @@ extern "C" lra_status lra_sampling_table_noalloc(lra_ctx *ctx, int64_t n, const 
         const cudaStream_t s = ctx->stream;
         const int64_t words = ceil_div(n, 256) + 16;
         double *sm = reinterpret_cast<double *>(scr + kScratchWords - 8);  // sum, max, kappa
-        // the array keeps the previous call's contents: clear what this call uses
-        LRA_CUDA(cudaMemsetAsync(scr, 0, sizeof(uint64_t) * words, s));
-        LRA_CUDA(cudaMemsetAsync(sm, 0, sizeof(double) * 4, s));
+        // The array keeps the previous call's contents.  Every word this call
+        // reads is written first by this call (tile sums, block maxima, and the
+        // sum, max and kappa slots), so nothing needs clearing.
+        (void)words;
         sum_max(s, norm2, n, sm, nullptr);
         sampling_table(s, norm2, n, mode, sm + 1, cum, c, sm + 2, scr);
         uint64_t tot = 0;
-        double kp = 0.0;
+        double kp = 0.0, sum = 0.0;
         LRA_CUDA(cudaMemcpyAsync(&tot, cum + n - 1, sizeof(tot), cudaMemcpyDeviceToHost, s));
         LRA_CUDA(cudaMemcpyAsync(&kp, sm + 2, sizeof(kp), cudaMemcpyDeviceToHost, s));
+        LRA_CUDA(cudaMemcpyAsync(&sum, sm, sizeof(sum), cudaMemcpyDeviceToHost, s));
         LRA_CUDA(cudaStreamSynchronize(s));
+        if (!std::isfinite(sum)) {
+            set_error("a column norm is not finite");
+            return LRA_EINVAL;
+        }
         if (total) *total = tot;
         if (kappa) *kappa = kp;
         return LRA_OK;

@@ -97,7 +97,9 @@ __global__ void weights_kernel(const double *__restrict__ norm2, int64_t n, int 
     const double mx = *maxn;
     const double v = norm2[i];
     uint64_t wi = 0;
-    if (v > 0.0 && mx > 0.0) {
+    // a non-finite norm (or maximum) gets no weight; the callers reject such
+    // input from the FP64 sum of the norms
+    if (v > 0.0 && mx > 0.0 && isfinite(v) && isfinite(mx)) {
         const double scale = __ddiv_rn(4294967296.0, mx);
         const double f = floor(__dmul_rn(v, scale));
         wi = (uint64_t)f;

@@ -28,9 +28,9 @@ int env_int(const char *name, int dflt) {
 Server::Server(lra_ctx *ctx, int slots) : ctx_(ctx) {
     size_t free_b = 0, total_b = 0;
     LRA_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    // what the loop may hand out: the context budget if set, else 90% of what is free now
-    capacity_ = ctx->budget ? (ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0)
-                            : (size_t)(0.9 * (double)free_b);
+    // the most the context may hold: its budget if set, else what it holds now
+    // plus 90% of what is free now
+    limit_ = ctx->budget ? ctx->budget : ctx->used.load() + (size_t)(0.9 * (double)free_b);
     streams_.resize(slots);
     for (int i = 0; i < slots; ++i) LRA_CUDA(cudaStreamCreateWithFlags(&streams_[i], cudaStreamNonBlocking));
     for (int i = 0; i < slots; ++i) threads_.emplace_back(&Server::worker, this, i);
@@ -54,18 +54,53 @@ Server::~Server() {
     for (auto s : streams_) cudaStreamDestroy(s);
 }
 
-size_t Server::capacity_locked() const { return capacity_ > reserved_ ? capacity_ - reserved_ : 0; }
+// What the loop could hand out with no job running: the limit minus the
+// context's memory outside the running jobs (matrices, their sampling tables,
+// unpolled results), read at the time of the call, so that matrices created
+// after the loop started are accounted for.
+size_t Server::idle_capacity_locked() const {
+    const size_t used = ctx_->used.load();
+    const size_t outside = used > job_bytes_ ? used - job_bytes_ : 0;
+    return limit_ > outside ? limit_ - outside : 0;
+}
+
+size_t Server::capacity_locked() const {
+    const size_t idle = idle_capacity_locked();
+    return idle > reserved_ ? idle - reserved_ : 0;
+}
 
 // First queued job (in arrival order) whose footprint fits; nullptr if none.
+// With no job running, a queued job larger than the idle capacity (matrices
+// created after it was queued took the memory) can never start: it ends with
+// LRA_ENOMEM instead of waiting forever.
 std::shared_ptr<Job> Server::admit_locked() {
+    const size_t cap = capacity_locked();
     for (auto it = queue_.begin(); it != queue_.end(); ++it) {
-        if ((*it)->footprint <= capacity_locked()) {
+        if ((*it)->footprint <= cap) {
             auto j = *it;
             queue_.erase(it);
             reserved_ += j->footprint;
             j->state = Job::RUNNING;
             return j;
         }
+    }
+    if (reserved_ == 0) {
+        const size_t idle = idle_capacity_locked();
+        bool failed = false;
+        for (auto it = queue_.begin(); it != queue_.end();) {
+            if ((*it)->footprint > idle) {
+                auto j = *it;
+                it = queue_.erase(it);
+                j->state = Job::DONE;
+                j->status = LRA_ENOMEM;
+                j->error = "job footprint exceeds the device memory left to the request loop";
+                j->mat->busy.fetch_sub(1);
+                failed = true;
+            } else {
+                ++it;
+            }
+        }
+        if (failed) cv_done_.notify_all();
     }
     return nullptr;
 }
@@ -93,6 +128,13 @@ void Server::worker(int slot) {
                 j->stream = s;
                 j->U = static_cast<float *>(dev_alloc(ctx_, j->U_bytes, s));
                 j->ritz = static_cast<double *>(dev_alloc(ctx_, j->ritz_bytes, s));
+                {
+                    size_t held = j->U_bytes + j->ritz_bytes;
+                    for (const auto &a : ws.allocs) held += a.second;
+                    std::lock_guard<std::mutex> g(mu_);
+                    j->held = held;
+                    job_bytes_ += held;
+                }
                 Engine e(j->mat, ws, s);
                 std::memset(&j->rep, 0, sizeof(j->rep));
                 j->rep.struct_size = sizeof(j->rep);
@@ -113,6 +155,8 @@ void Server::worker(int slot) {
             j->rep.status = st;
             j->state = Job::DONE;
             reserved_ -= j->footprint;
+            job_bytes_ -= j->held;  // the workspace is freed; unpolled results count as outside memory
+            j->held = 0;
             j->mat->busy.fetch_sub(1);
         }
         cv_done_.notify_all();
@@ -134,7 +178,7 @@ lra_status Server::submit(lra_mat *mat, int k, int p, double eps, uint64_t seed,
     j->footprint = job_footprint(mat, k, p, o);
     {
         std::lock_guard<std::mutex> g(mu_);
-        if (j->footprint > capacity_) {
+        if (j->footprint > idle_capacity_locked()) {
             set_error("job footprint exceeds the device memory available to the request loop");
             return LRA_ENOMEM;
         }

@@ -35,6 +35,7 @@ struct Job {
     float *U = nullptr;      // device, d x k (column-major, leading dim d)
     double *ritz = nullptr;  // device, k
     size_t U_bytes = 0, ritz_bytes = 0;
+    size_t held = 0;          // bytes counted in Server::job_bytes_ while the job runs
     lra_report rep{};
     std::string error;
 };
@@ -50,6 +51,7 @@ class Server {
    private:
     void worker(int slot);
     std::shared_ptr<Job> admit_locked();
+    size_t idle_capacity_locked() const;
     size_t capacity_locked() const;
 
     lra_ctx *ctx_;
@@ -58,7 +60,8 @@ class Server {
     std::deque<std::shared_ptr<Job>> queue_;
     std::map<lra_job, std::shared_ptr<Job>> jobs_;
     size_t reserved_ = 0;    // footprints of running jobs
-    size_t capacity_ = 0;    // device bytes the loop may hand out
+    size_t limit_ = 0;       // device bytes the context may reach (budget, or used + 90% of free at start)
+    size_t job_bytes_ = 0;   // bytes the running jobs hold (workspace and result buffers)
     lra_job next_id_ = 1;
     bool stop_ = false;
     std::vector<std::thread> threads_;

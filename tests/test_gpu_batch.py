@@ -156,9 +156,9 @@ def test_batch_errors(ctx):
 
 @pytest.mark.parametrize("bad", [float("nan"), float("inf")])
 def test_non_finite_dense_input_returns_a_status(ctx, bad):
-    """A NaN or Inf entry in a dense X ends the solve with a status (divergence at
-    the first anchor, a failed Cholesky, or no sampleable column), and the
-    context still solves the next matrix."""
+    """A NaN or Inf entry in a dense X makes ||X||_F^2 non-finite: the solve
+    returns LRA_EINVAL before any iteration, and the context still solves the
+    next matrix."""
     d, n = 256, 800
     Xt = planted(d, n, 3, 5)
     Xbad = Xt.copy()
@@ -169,7 +169,7 @@ def test_non_finite_dense_input_returns_a_status(ctx, bad):
     m = lra.lra_create_dense(ctx, d, n, lra.LRA_F32, Xbad, d, False, lra.LRA_F32)
     try:
         st = lra.lib.lra_solve(m, 3, 6, 1e-3, 0, ctypes.byref(o), U.data_ptr(), r.data_ptr(), None)
-        assert st in (1, 5, 6)
+        assert st == 1
     finally:
         lra.lra_mat_destroy(m)
     m = lra.lra_create_dense(ctx, d, n, lra.LRA_F32, Xt, d, False, lra.LRA_F32)

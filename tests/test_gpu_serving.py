@@ -114,3 +114,46 @@ def test_job_beyond_the_memory_budget_is_rejected():
         lra.lra_mat_destroy(m)
     finally:
         lra.lra_finalize(ctx)
+
+
+def test_admission_sees_matrices_created_after_the_loop_started():
+    """The loop's capacity is read at admission time: after a matrix created
+    later takes nearly all of the context's budget, a job that fitted before
+    is refused with LRA_ENOMEM instead of failing part-way through its solve."""
+    import ctypes
+    ctx = lra.lra_init(0, 24 << 20)
+    mats = []
+    try:
+        m = _mat(ctx, 256, 4096, 5, 3, lra.LRA_F32)
+        mats.append(m)
+        opt = lra.options(shift_policy=lra.LRA_SHIFT_FAR)
+        U = torch.zeros(5, 256, device="cuda")
+        r = torch.zeros(5, dtype=torch.float64, device="cuda")
+        first = lra.lra_submit(ctx, m, 5, 10, 1e-3, 1, opt)
+        assert lra.lra_poll(ctx, first, -1, U, r) == 0
+        # the largest matrix that still fits the budget (200 KB steps), leaving
+        # less than any job's workspace
+        sig = L.sigma_serving(5, 256)
+        for n2 in range(8000, 200, -100):
+            Xt, _, _ = L.planted_numpy(256, n2, sig, 9)
+            Xd = torch.from_numpy(np.ascontiguousarray(Xt.astype(np.float32))).cuda()  # no staging copy
+            h = ctypes.c_void_p()
+            st = lra.lib.lra_create_dense(ctx, 256, n2, lra.LRA_F32, Xd.data_ptr(), 256, 1, lra.LRA_F32,
+                                          ctypes.byref(h))
+            del Xd
+            if st == 0:
+                mats.append(h)
+                break
+            assert st == LRA_ENOMEM
+        assert len(mats) == 2
+        job = ctypes.c_uint64()
+        st = lra.lib.lra_submit(ctx, m, 5, 10, 1e-3, 1, ctypes.byref(opt), ctypes.byref(job))
+        assert st == LRA_ENOMEM
+        # destroying the big matrix gives the memory back to the loop
+        lra.lra_mat_destroy(mats.pop())
+        again = lra.lra_submit(ctx, m, 5, 10, 1e-3, 1, opt)
+        assert lra.lra_poll(ctx, again, -1, U, r) == 0
+    finally:
+        for h in mats:
+            lra.lra_mat_destroy(h)
+        lra.lra_finalize(ctx)

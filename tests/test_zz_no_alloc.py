@@ -56,6 +56,30 @@ def test_noalloc_table_equals_allocating_table_on_consecutive_calls():
         lra.lra_finalize(ctx)
 
 
+def test_noalloc_table_allocates_nothing():
+    """On a context whose device-memory budget is one byte every allocation of
+    the library fails with LRA_ENOMEM (the allocating builder shows it); the
+    no-allocation builder still succeeds there, on two calls in a row, with the
+    allocating builder's results from an unconstrained context."""
+    ref_ctx = lra.lra_init(0)
+    tiny = lra.lra_init(0, 1)
+    try:
+        for n, mode, seed in [(5000, lra.LRA_SAMPLE_IMPORTANCE, 7), (123457, lra.LRA_SAMPLE_IMPORTANCE, 8)]:
+            norm2 = _norms(n, seed)
+            nd = torch.from_numpy(norm2).cuda()
+            cum = torch.zeros(n, dtype=torch.int64, device="cuda")
+            c = torch.zeros(n, dtype=torch.float32, device="cuda")
+            st = lra.lib.lra_sampling_table(tiny, n, nd.data_ptr(), mode, cum.data_ptr(), c.data_ptr(), None, None)
+            assert st == 2  # LRA_ENOMEM: the budget refuses any allocation
+            ref = _table(lra.lra_sampling_table, ref_ctx, norm2, mode)
+            got = _table(lra.lra_sampling_table_noalloc, tiny, norm2, mode)
+            assert got[0] == ref[0] and got[1] == ref[1]
+            assert np.array_equal(got[2], ref[2]) and np.array_equal(got[3], ref[3])
+    finally:
+        lra.lra_finalize(tiny)
+        lra.lra_finalize(ref_ctx)
+
+
 def test_noalloc_table_rejects_sizes_beyond_its_array():
     ctx = lra.lra_init(0)
     try:
