@@ -128,6 +128,11 @@ typedef struct lra_options {
                                Delta (or p + 1 <= LRA_MAX_P to estimate it); shift_policy is
                                not used.  Default 0 (the q = k branch at s = 1). */
     int part_max_iters;     /* cap on Algorithm 3's ceil(eps'^-1 ln(d/eps')) iterations; default 2000 */
+    int64_t wait_cycles;    /* lra_solve: a pipeline wait of the tensor-core X passes that has not
+                               completed after this many SM cycles gives up; the kernel unwinds
+                               (waiting, with the default limit, for its own copies and MMAs in
+                               flight) and the solve returns LRA_ETIMEOUT.  0 = 4e9 cycles
+                               (about 2 s).  Not from the paper: a failure-handling knob. */
 } lra_options;
 
 typedef struct lra_report {

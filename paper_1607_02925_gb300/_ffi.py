@@ -61,6 +61,7 @@ class LraOptions(C.Structure):
         ("acc_target", C.c_int64),
         ("partition", C.c_int),
         ("part_max_iters", C.c_int),
+        ("wait_cycles", C.c_int64),
     ]
 
 

@@ -138,6 +138,7 @@ void lra_options_default(lra_options *opt) {
     opt->acc_target = 0;
     opt->partition = 0;
     opt->part_max_iters = 2000;
+    opt->wait_cycles = 0;
 }
 
 const char *lra_status_str(lra_status s) {

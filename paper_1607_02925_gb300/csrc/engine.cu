@@ -74,13 +74,15 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
         r.acc_target = o->acc_target;
         r.partition = o->partition;
         r.part_max_iters = o->part_max_iters;
+        r.wait_cycles = o->wait_cycles;
     }
     if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
     if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
         r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
         r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0) || r.batch < 1 || r.batch > 16 ||
         (r.batch & (r.batch - 1)) != 0 || r.acc < 0 || r.acc > 1 || !(r.acc_theta > 0.0 && r.acc_theta <= 1.0) ||
-        r.acc_max_outer < 1 || r.acc_target < 0 || r.partition < 0 || r.partition > 1 || r.part_max_iters < 1) {
+        r.acc_max_outer < 1 || r.acc_target < 0 || r.partition < 0 || r.partition > 1 || r.part_max_iters < 1 ||
+        r.wait_cycles < 0) {
         set_error("invalid lra_options field");
         throw Error{LRA_EINVAL};
     }
@@ -335,7 +337,7 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo)
         // the BF16 hi/lo copy of Y feeds a following X Y pass; an FP32 result
         // (Rayleigh-Ritz, the power steps) is used alone unless keep_hilo
         xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, (Y && !keep_hilo) ? nullptr : ws_.Yb,
-               ws_.ldy, ws_.tcerr);
+               ws_.ldy, ws_.tcerr, tc_wait_);
         if (timer) timer->end();
     } else {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
@@ -359,7 +361,7 @@ void Engine::xy_pass(const float *Y32, int p, bool use32) {
         if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
         ws_.nch = xy_chunks(mat_->dpad, mat_->n, tc_rows_per_cta(PP, mat_->Xl != nullptr));
         if (timer) timer->begin(KernelTimer::XY, p);
-        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp, ws_.nch, ws_.tcerr);
+        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp, ws_.nch, ws_.tcerr, tc_wait_);
         if (timer) timer->end();
     } else {
         ws_.nch = xy_chunks(mat_->dpad, mat_->n, 128);
@@ -690,6 +692,7 @@ double Engine::lambda1_estimate(uint64_t seed) {
     gram(s_, ws_.Y, mat_->n, pad_p(1), 1, 1, ws_.Gm, ws_.gscr);
     LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.Gm, sizeof(double), cudaMemcpyDeviceToHost, s_));
     sync();
+    if (tc(false)) check_tc();
     return ws_.host[0];
 }
 
@@ -1034,6 +1037,7 @@ lra_status Engine::solve(int k, int p, double eps, uint64_t seed, const Opts &o,
     const auto t_all = std::chrono::steady_clock::now();
     const int64_t launches0 = launches_of_thread();
     const int64_t d = mat_->d, dpad = mat_->dpad;
+    tc_wait_ = o.wait_cycles;
     std::unique_ptr<KernelTimer> own_timer;
     if (o.profile) {
         own_timer.reset(new KernelTimer(s_));

@@ -87,6 +87,7 @@ struct Opts {
     int64_t acc_target = 0;    // samples per epoch the proximal weight aims for; 0 = n
     int partition = 0;         // 1: Algorithm 6 with adaptive partitioning and deflation
     int part_max_iters = 2000; // cap on Algorithm 3's iteration count
+    int64_t wait_cycles = 0;   // tensor-core pipeline wait limit (0 = the kernels' default)
 };
 
 // CUDA-event timing of individual kernel launches on the engine's stream.
@@ -279,6 +280,7 @@ class Engine {
     void check_tc();  // raise if a tensor-core kernel reported a timed-out wait
     Stats stats;
     KernelTimer *timer = nullptr;
+    long long tc_wait_ = 0;  // pipeline wait limit of the tensor-core passes (0 = default)
 
    private:
     // tensor-core passes: BF16 X, or the BF16 pair of an FP32 X; the exact FP32

@@ -59,11 +59,23 @@ struct Tile {
 
 constexpr int kThreads = 192;  // producer warp, MMA warp, four epilogue warps
 
-// Control block after the stages: ring barriers, accumulator barriers, TMEM address.
+// Control block after the stages: ring barriers, accumulator barriers, the
+// MMA issuer's unwinding barrier, TMEM address.
 struct Ctl {
-    uint64_t full[6], empty[6], accf[2], acce[2];
+    uint64_t full[6], empty[6], accf[2], acce[2], mmadone;
     uint32_t tmem;
 };
+
+// K blocks accumulated into one TMEM accumulator before the epilogue reads it
+// out and adds it in FP32 registers (round to nearest).  The tensor core's
+// FP32 accumulation does not round to nearest: every MMA shortens the running
+// sum slightly toward zero, a bias that grows with the number of MMAs into one
+// accumulator (about 1.3e-5 relative after the 768 MMAs of a 4096-long FP32
+// pair product).  Restarting the accumulator every 4 K blocks (48 MMAs) keeps
+// that bias near 1e-6 for the FP32 pair; BF16 X (relative tolerance 1e-2)
+// keeps one accumulator per tile.
+template <int NA>
+__host__ __device__ constexpr int seg_kb() { return NA == 2 ? 4 : (1 << 30); }
 
 template <int PP, int NA, int MT>
 __device__ __forceinline__ void init_ctl(Ctl *ctl) {
@@ -76,6 +88,7 @@ __device__ __forceinline__ void init_ctl(Ctl *ctl) {
         mbar_init(&ctl->accf[b], 1);
         mbar_init(&ctl->acce[b], 4);  // one arrival per epilogue warp
     }
+    mbar_init(&ctl->mmadone, 1);
     fence_barrier_init();
 }
 
@@ -87,6 +100,13 @@ __device__ __forceinline__ void drain_issued(Ctl *ctl, int issued) {
         mbar_wait(&ctl->full[g % S], (uint32_t)(g / S) & 1u);
 }
 
+// After an error the MMA issuer waits (bounded) until every MMA it issued has
+// completed, so that none writes TMEM once the CTA frees it.
+__device__ __forceinline__ void drain_mmas(Ctl *ctl) {
+    mma_commit(&ctl->mmadone);
+    mbar_wait(&ctl->mmadone, 0u);
+}
+
 // ---------------------------------------------------------------------------
 // Y = X^T W: work tile = MT x 128 data points (rows of X^T), K = d
 // ---------------------------------------------------------------------------
@@ -96,9 +116,10 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
                                                              const __grid_constant__ CUtensorMap tmW,
                                                              int nkb, int64_t n, float *__restrict__ Y32,
                                                              __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
-                                                             int *__restrict__ err) {
+                                                             int *__restrict__ err, long long lim) {
     using T = Tile<PP, NA, MT>;
     constexpr int S = T::kStages;
+    constexpr int KS = seg_kb<NA>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + S * T::kStage);
@@ -128,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
             const int64_t i0 = (int64_t)tile * kBM * MT;
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int st = g % S;
-                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u)) {
+                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u, lim)) {
                     atomicOr(err, kErrTimeout);
                     ok = false;
                     break;
@@ -147,88 +168,127 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
         }
         if (!ok) drain_issued<S>(ctl, g);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: tile lt accumulates into set lt & 1
+        // MMA issuer: the K blocks of a tile form segments of KS; segment sc
+        // (counted over the CTA's whole walk) accumulates into set sc & 1
         constexpr uint32_t idesc = instr_desc(1, 0, 0, PP, kBM);
-        int g = 0, lt = 0;
+        int g = 0, sc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
-            if (lt >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((lt >> 1) - 1) & 1u)) {
-                atomicOr(err, kErrTimeout);
-                break;
-            }
-            tc_fence_after();
-            const uint32_t accb = tmem + buf * T::kAccCols;
-            for (int kb = 0; kb < nkb; ++kb, ++g) {
-                const int st = g % S;
-                if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u)) {
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int s0 = 0; s0 < nkb && ok; s0 += KS, ++sc) {
+                const int buf = sc & 1;
+                if (sc >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((sc >> 1) - 1) & 1u, lim)) {
                     atomicOr(err, kErrTimeout);
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a = smem_u32(smem + st * T::kStage);
-                const uint32_t bh = a + T::kA, bl = bh + T::kB;
-#pragma unroll
-                for (int ks = 0; ks < kBK / 16; ++ks) {
-                    const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                    const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const uint32_t am = a + mt * T::kA1;
-                        const uint32_t acc = accb + mt * kAccCols1;
-                        const uint64_t ad = sw128_desc(am + ks * 32, 16, 1024);
-                        mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
-                        mma_f16(acc, ad, bld, idesc, 1u);
-                        if (NA == 2) mma_f16(acc, sw128_desc(am + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+                const uint32_t accb = tmem + buf * T::kAccCols;
+                const int s1 = (nkb - s0 < KS) ? nkb : s0 + KS;
+                for (int kb = s0; kb < s1; ++kb, ++g) {
+                    const int st = g % S;
+                    if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u, lim)) {
+                        atomicOr(err, kErrTimeout);
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(smem + st * T::kStage);
+                    const uint32_t bh = a + T::kA, bl = bh + T::kB;
+#pragma unroll
+                    for (int ks = 0; ks < kBK / 16; ++ks) {
+                        const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                        const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            const uint32_t am = a + mt * T::kA1;
+                            const uint32_t acc = accb + mt * kAccCols1;
+                            const uint64_t ad = sw128_desc(am + ks * 32, 16, 1024);
+                            mma_f16(acc, ad, bhd, idesc, ((kb - s0) | ks) != 0);
+                            mma_f16(acc, ad, bld, idesc, 1u);
+                            if (NA == 2) mma_f16(acc, sw128_desc(am + kATile + ks * 32, 16, 1024), bhd, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&ctl->empty[st]);
                 }
-                mma_commit(&ctl->empty[st]);
+                if (ok) mma_commit(&ctl->accf[buf]);
             }
-            if (ok) mma_commit(&ctl->accf[buf]);
         }
+        if (!ok) drain_mmas(ctl);
     } else if (warp >= 2) {
-        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 of both M tiles
+        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 of every M tile
         const int q = warp & 3;
-        int lt = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
-            if (!mbar_wait(&ctl->accf[buf], (uint32_t)(lt >> 1) & 1u)) {
-                if (lane == 0) atomicOr(err, kErrTimeout);
-                break;
+        int sc = 0;
+        bool ok = true;
+        auto store = [&](int64_t i, int c, const float *v) {
+            if (i >= n) return;
+            if (Y32) {
+                float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
             }
-            tc_fence_after();
-            const int64_t i0 = (int64_t)tile * kBM * MT;
-#pragma unroll 1
-            for (int mt = 0; mt < MT; ++mt) {
-                const int64_t i = i0 + mt * kBM + q * 32 + lane;
-                const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
+            if (Yb) {
 #pragma unroll
-                for (int c = 0; c < PP; c += 16) {
-                    float v[16];
-                    tmem_ld16(tl + c, v);
-                    if (i < n) {
-                        if (Y32) {
-                            float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-                                dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-                        }
-                        if (Yb) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
-                                const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
-                                Yb[(int64_t)(c + j) * ldy + i] = hi;
-                                Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
-                            }
-                        }
-                    }
+                for (int j = 0; j < 16; ++j) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                    Yb[(int64_t)(c + j) * ldy + i] = hi;
+                    Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->acce[buf]);
+        };
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t i0 = (int64_t)tile * kBM * MT;
+            if constexpr (NA == 2) {
+                // MT = 1: the segments' partial sums are added in registers
+                float accv[PP];
+                for (int s0 = 0; s0 < nkb; s0 += KS, ++sc) {
+                    const int buf = sc & 1;
+                    if (!mbar_wait(&ctl->accf[buf], (uint32_t)(sc >> 1) & 1u, lim)) {
+                        if (lane == 0) atomicOr(err, kErrTimeout);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols;
+#pragma unroll
+                    for (int c = 0; c < PP; c += 16) {
+                        float v[16];
+                        tmem_ld16(tl + c, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) accv[c + j] = (s0 == 0) ? v[j] : accv[c + j] + v[j];
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl->acce[buf]);
+                }
+                if (!ok) break;
+                const int64_t i = i0 + q * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < PP; c += 16) store(i, c, accv + c);
+            } else {
+                // one segment per tile
+                const int buf = sc & 1;
+                if (!mbar_wait(&ctl->accf[buf], (uint32_t)(sc >> 1) & 1u, lim)) {
+                    if (lane == 0) atomicOr(err, kErrTimeout);
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int64_t i = i0 + mt * kBM + q * 32 + lane;
+                    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
+#pragma unroll
+                    for (int c = 0; c < PP; c += 16) {
+                        float v[16];
+                        tmem_ld16(tl + c, v);
+                        store(i, c, v);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->acce[buf]);
+                ++sc;
+            }
         }
     }
     tc_fence_before();
@@ -250,9 +310,10 @@ __global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tmY,
                                                             int64_t cols_per_chunk, int nchunks, int64_t n,
                                                             int64_t dpad, float *__restrict__ Gp,
-                                                            int *__restrict__ err) {
+                                                            int *__restrict__ err, long long lim) {
     using T = Tile<PP, NA, MT>;
     constexpr int S = T::kStages;
+    constexpr int KS = seg_kb<NA>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + S * T::kStage);
@@ -291,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constan
             const int nkb = chunk_kb(ch, c0);
             for (int kb = 0; kb < nkb; ++kb, ++g) {
                 const int st = g % S;
-                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u)) {
+                if (g >= S && !mbar_wait(&ctl->empty[st], ((uint32_t)(g / S) & 1u) ^ 1u, lim)) {
                     atomicOr(err, kErrTimeout);
                     ok = false;
                     break;
@@ -317,88 +378,137 @@ __global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constan
         }
         if (!ok) drain_issued<S>(ctl, g);
     } else if (warp == 1 && lane == 0) {
+        // MMA issuer: segments of KS K blocks; segment sc accumulates into set
+        // sc & 1 (an empty chunk is one empty segment, drained as zeros)
         constexpr uint32_t idesc = instr_desc(1, 1, 0, PP, kBM);
-        int g = 0, lt = 0;
+        int g = 0, sc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             int64_t c0;
             const int nkb = chunk_kb(tile / rtiles, c0);
-            if (lt >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((lt >> 1) - 1) & 1u)) {
-                atomicOr(err, kErrTimeout);
-                break;
-            }
-            tc_fence_after();
-            const uint32_t accb = tmem + buf * T::kAccCols;
-            for (int kb = 0; kb < nkb; ++kb, ++g) {
-                const int st = g % S;
-                if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u)) {
+            const int nseg = nkb > 0 ? (nkb + KS - 1) / KS : 1;
+            for (int sg = 0; sg < nseg && ok; ++sg, ++sc) {
+                const int buf = sc & 1;
+                if (sc >= 2 && !mbar_wait(&ctl->acce[buf], (uint32_t)((sc >> 1) - 1) & 1u, lim)) {
                     atomicOr(err, kErrTimeout);
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a = smem_u32(smem + st * T::kStage);
-                const uint32_t bh = a + T::kA, bl = bh + T::kB;
-#pragma unroll
-                for (int ks = 0; ks < kBK / 16; ++ks) {
-                    const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
-                    const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
-                        const uint32_t am = a + mt * T::kA1;
-                        const uint32_t acc = accb + mt * kAccCols1;
-                        const uint64_t ad = sw128_desc(am + ks * 2048, kATile / 2, 1024);
-                        mma_f16(acc, ad, bhd, idesc, (kb | ks) != 0);
-                        mma_f16(acc, ad, bld, idesc, 1u);
-                        if (NA == 2)
-                            mma_f16(acc, sw128_desc(am + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                const uint32_t accb = tmem + buf * T::kAccCols;
+                const int s0 = sg * KS;
+                const int s1 = (nkb - s0 < KS) ? nkb : s0 + KS;
+                for (int kb = s0; kb < s1; ++kb, ++g) {
+                    const int st = g % S;
+                    if (!mbar_wait(&ctl->full[st], (uint32_t)(g / S) & 1u, lim)) {
+                        atomicOr(err, kErrTimeout);
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(smem + st * T::kStage);
+                    const uint32_t bh = a + T::kA, bl = bh + T::kB;
+#pragma unroll
+                    for (int ks = 0; ks < kBK / 16; ++ks) {
+                        const uint64_t bhd = sw128_desc(bh + ks * 32, 16, 1024);
+                        const uint64_t bld = sw128_desc(bl + ks * 32, 16, 1024);
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            // A: 64-row MN blocks 8 KB apart, 8-column K groups 1 KB apart
+                            const uint32_t am = a + mt * T::kA1;
+                            const uint32_t acc = accb + mt * kAccCols1;
+                            const uint64_t ad = sw128_desc(am + ks * 2048, kATile / 2, 1024);
+                            mma_f16(acc, ad, bhd, idesc, ((kb - s0) | ks) != 0);
+                            mma_f16(acc, ad, bld, idesc, 1u);
+                            if (NA == 2)
+                                mma_f16(acc, sw128_desc(am + kATile + ks * 2048, kATile / 2, 1024), bhd, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&ctl->empty[st]);
                 }
-                mma_commit(&ctl->empty[st]);
+                if (ok) mma_commit(&ctl->accf[buf]);
             }
-            if (ok) mma_commit(&ctl->accf[buf]);
         }
+        if (!ok) drain_mmas(ctl);
     } else if (warp >= 2) {
         const int q = warp & 3;
-        int lt = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
+        int sc = 0;
+        bool ok = true;
+        auto store = [&](float *out, int64_t r, int c, const float *v) {
+            if (r < dpad) {
+                float4 *dst = reinterpret_cast<float4 *>(out + c);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            }
+        };
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int rt = tile % rtiles, ch = tile / rtiles;
             int64_t c0;
             const int nkb = chunk_kb(ch, c0);
-            if (!mbar_wait(&ctl->accf[buf], (uint32_t)(lt >> 1) & 1u)) {
-                if (lane == 0) atomicOr(err, kErrTimeout);
-                break;
-            }
-            tc_fence_after();
+            const int nseg = nkb > 0 ? (nkb + KS - 1) / KS : 1;
             const int64_t r0 = (int64_t)rt * kBM * MT;
-#pragma unroll 1
-            for (int mt = 0; mt < MT; ++mt) {
-                const int64_t r = r0 + mt * kBM + q * 32 + lane;
-                float *out = Gp + (int64_t)ch * dpad * PP + r * PP;
-                const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
-#pragma unroll
-                for (int c = 0; c < PP; c += 16) {
-                    float v[16];
-                    if (nkb > 0) {
-                        tmem_ld16(tl + c, v);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 16; ++u) v[u] = 0.0f;
+            if constexpr (NA == 2) {
+                // MT = 1: the segments' partial sums are added in registers
+                float accv[PP];
+                for (int sg = 0; sg < nseg; ++sg, ++sc) {
+                    const int buf = sc & 1;
+                    if (!mbar_wait(&ctl->accf[buf], (uint32_t)(sc >> 1) & 1u, lim)) {
+                        if (lane == 0) atomicOr(err, kErrTimeout);
+                        ok = false;
+                        break;
                     }
-                    if (r < dpad) {
-                        float4 *dst = reinterpret_cast<float4 *>(out + c);
+                    tc_fence_after();
+                    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                    for (int c = 0; c < PP; c += 16) {
+                        float v[16];
+                        if (nkb > 0) {
+                            tmem_ld16(tl + c, v);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) v[u] = 0.0f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) accv[c + j] = (sg == 0) ? v[j] : accv[c + j] + v[j];
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl->acce[buf]);
+                }
+                if (!ok) break;
+                const int64_t r = r0 + q * 32 + lane;
+                float *out = Gp + (int64_t)ch * dpad * PP + r * PP;
+#pragma unroll
+                for (int c = 0; c < PP; c += 16) store(out, r, c, accv + c);
+            } else {
+                const int buf = sc & 1;
+                if (!mbar_wait(&ctl->accf[buf], (uint32_t)(sc >> 1) & 1u, lim)) {
+                    if (lane == 0) atomicOr(err, kErrTimeout);
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int64_t r = r0 + mt * kBM + q * 32 + lane;
+                    float *out = Gp + (int64_t)ch * dpad * PP + r * PP;
+                    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + buf * T::kAccCols + mt * kAccCols1;
+#pragma unroll
+                    for (int c = 0; c < PP; c += 16) {
+                        float v[16];
+                        if (nkb > 0) {
+                            tmem_ld16(tl + c, v);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) v[u] = 0.0f;
+                        }
+                        store(out, r, c, v);
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->acce[buf]);
+                ++sc;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->acce[buf]);
         }
     }
     tc_fence_before();
@@ -535,7 +645,9 @@ void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh
 int tc_rows_per_cta(int PP, bool pair) { return (!pair && PP >= 64) ? 2 * kBM : kBM; }
 
 void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err) {
+            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err,
+            long long wait_cycles) {
+    const long long lim = wait_cycles > 0 ? wait_cycles : kWaitCycles;
     const CUtensorMap mx = make_map(X, dpad, n, dpad, kBK, kBM);
     const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, kBK, kBM);
     const CUtensorMap mw = make_map(Wb, dpad, 2 * PP, dpad, kBK, PP);
@@ -546,7 +658,7 @@ void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, rows), sm_count());
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<grid, kThreads, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err);
+            kern<<<grid, kThreads, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err, lim);
             LRA_LAUNCHED();
         };
         if (Xl)
@@ -559,7 +671,9 @@ void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int
 }
 
 void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err) {
+           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err,
+           long long wait_cycles) {
+    const long long lim = wait_cycles > 0 ? wait_cycles : kWaitCycles;
     const CUtensorMap mx = make_map(X, dpad, n, dpad, 64, kBK);
     const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, 64, kBK);
     const CUtensorMap my = make_map(Yb, n, 2 * PP, ldy, kBK, PP);
@@ -570,7 +684,7 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(dpad, rows) * nchunks, sm_count());
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<grid, kThreads, smem, s>>>(mx, mxl, my, cpc, nchunks, n, dpad, Gp, err);
+            kern<<<grid, kThreads, smem, s>>>(mx, mxl, my, cpc, nchunks, n, dpad, Gp, err, lim);
             LRA_LAUNCHED();
         };
         if (Xl)

@@ -341,6 +341,217 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
     }
 }
 
+// One sample per step on NT = 32 NW threads (d > 512), two steps per block
+// barrier.  With Delta_{t+1} = a Delta_t + c_t x_t - eta M, the look-ahead
+// identity of svrg_inner_pair_kernel,
+//   r_{t+1} = a x_{t+1}^T Delta_t + c_t x_{t+1}^T x_t - x_{t+1}^T (eta M),
+// lets the dot products of steps t + 1 and t + 2 (the latter taken on
+// Delta_{t+1} once c_t is known, less its c_{t+1} term) share one block
+// reduction.  Each warp reduces its partial sums by shuffles; lane 0 writes
+// them to a shared row of 16 per value (zero for absent warps), and every
+// thread sums the 16 in a fixed order from four 16-byte loads.  Thread t owns
+// rows 4 (t + s NT) + v; the ring holds R columns, fetched R - 1 steps ahead,
+// and each thread copies and reads only its own rows of them.
+template <int N>
+__device__ __forceinline__ void block_sum16(float (&v)[N], float (*red)[16], int lane, int warp) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[i][warp] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float4 *q = reinterpret_cast<const float4 *>(red[i]);
+        const float4 a = q[0], b = q[1], c = q[2], d = q[3];
+        v[i] = (((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w))) +
+               (((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w)));
+    }
+}
+
+// Ring depth of the look-ahead kernel: the deepest of 8, 6, 4, 3 columns of
+// up to 2048 S rows that fits the shared-memory budget.
+template <typename TX, int S>
+__host__ __device__ constexpr int la_ring() {
+    constexpr size_t col = (size_t)2048 * S * sizeof(TX);
+    return 8 * col <= 220 * 1024 ? 8 : 6 * col <= 220 * 1024 ? 6 : 4 * col <= 220 * 1024 ? 4 : 3;
+}
+
+template <typename TX, int S, int PC, int R = la_ring<TX, S>()>
+__global__ void __launch_bounds__(512) svrg_inner_la_kernel(
+    const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
+    const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
+    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    constexpr int NV = 4 * PC + 2;  // uA, wA, uB, wB per column, then vA, vB
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX *ring = reinterpret_cast<TX *>(smem_raw);  // [R][dpad]
+    __shared__ __align__(16) float red[3][NV][16];
+
+    const int tid = threadIdx.x;
+    const int NT = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int j0 = blockIdx.x * PC;
+    constexpr int BYTES = 4 * sizeof(TX);
+
+    for (int e = tid; e < 3 * NV * 16; e += NT) (&red[0][0][0])[e] = 0.0f;
+
+    float dl[S][4][PC];   // Delta = W - Wt
+    float mm[S][4][PC];   // eta * M
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            const bool ok = (r < dpad) && (j0 + j < p);
+            const int64_t off = r + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                dl[s][v][j] = ok ? (W[off + v] - Wt[off + v]) : 0.0f;
+                mm[s][v][j] = ok ? eta * M[off + v] : 0.0f;
+            }
+        }
+    }
+
+    auto prefetch = [&](int64_t t) {
+        if (t < m) {
+            const TX *col = X + (int64_t)idx[t] * ldx;
+            TX *slot = ring + (t % R) * dpad;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
+            }
+        }
+        cp_async_commit();
+    };
+    auto load = [&](int64_t t, float (&x)[S][4]) {
+        const TX *slot = ring + (t % R) * dpad;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
+            if (t < m && r < dpad) {
+                if constexpr (sizeof(TX) == 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
+                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
+                } else {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
+            }
+        }
+    };
+    // partial sums of y^T Delta and y^T (eta M) per column, and y^T z
+    auto dots = [&](const float (&y)[S][4], const float (&z)[S][4], float *u, float *w, float &vv) {
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    a0 = fmaf(y[s][v], dl[s][v][j], a0);
+                    a1 = fmaf(y[s][v], mm[s][v][j], a1);
+                }
+            u[j] = a0;
+            w[j] = a1;
+        }
+        float a2 = 0.0f;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a2 = fmaf(y[s][v], z[s][v], a2);
+        vv = a2;
+    };
+    auto update = [&](const float (&x)[S][4], const float (&c)[PC], float a) {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int j = 0; j < PC; ++j) dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(c[j], x[s][v], -mm[s][v][j]));
+    };
+
+#pragma unroll
+    for (int u = 0; u < R - 1; ++u) prefetch(u);
+    const float a = 1.0f - eta * lam;
+    float x0[S][4], x1[S][4], x2[S][4];
+    float r[PC];
+    cp_async_wait<R - 2>();
+    load(0, x0);
+    {
+        float v0[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc = fmaf(x0[s][v], dl[s][v][j], acc);
+            v0[j] = acc;
+        }
+        block_sum16<PC>(v0, red[2], lane, warp);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) r[j] = v0[j];
+    }
+    int buf = 0;
+    for (int64_t t = 0; t < m; t += 2, buf ^= 1) {
+        prefetch(t + R - 1);
+        prefetch(t + R);
+        cp_async_wait<R - 2>();
+        load(t + 1, x1);
+        load(t + 2, x2);
+        const float c0 = eta * cval[t];
+        const float c1v = (t + 1 < m) ? eta * cval[t + 1] : 0.0f;
+        float ct[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
+        float acc[NV];
+        // chain A: r_{t+1} from Delta_t
+        dots(x1, x0, acc, acc + PC, acc[4 * PC]);
+        // step t
+        update(x0, ct, a);
+        // chain B: r_{t+2} from Delta_{t+1}, less the c_{t+1} term
+        dots(x2, x1, acc + 2 * PC, acc + 3 * PC, acc[4 * PC + 1]);
+        block_sum16<NV>(acc, red[buf], lane, warp);
+        float c1[PC];
+#pragma unroll
+        for (int j = 0; j < PC; ++j) c1[j] = c1v * fmaf(a, acc[j], fmaf(ct[j], acc[4 * PC], -acc[PC + j]));
+        if (t + 1 < m) {
+            // step t + 1
+            update(x1, c1, a);
+#pragma unroll
+            for (int j = 0; j < PC; ++j)
+                r[j] = fmaf(a, acc[2 * PC + j], fmaf(c1[j], acc[4 * PC + 1], -acc[3 * PC + j]));
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) x0[s][v] = x2[s][v];
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int64_t r0 = 4 * ((int64_t)tid + (int64_t)s * NT);
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            if (r0 < dpad && j0 + j < p) {
+                const int64_t off = r0 + (int64_t)(j0 + j) * dpad;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) W[off + v] = Wt[off + v] + dl[s][v][j];
+            }
+        }
+    }
+}
+
 // A batch of NB > 1 samples per step: the stochastic term averaged over the
 // NB samples, every r_u taken at the same W.  One column per CTA; the ring
 // holds D steps of NB columns, D - 1 steps fetched ahead; each thread copies
@@ -523,6 +734,17 @@ void launch_inner1(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, in
     LRA_LAUNCHED();
 }
 
+template <typename TX, int S, int PC>
+void launch_la(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W, const float *Wt,
+               const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam, int nt) {
+    constexpr int R = la_ring<TX, S>();
+    auto k = svrg_inner_la_kernel<TX, S, PC, R>;
+    const size_t smem = (size_t)R * dpad * sizeof(TX);
+    ensure_smem(k, (int)smem);
+    k<<<(unsigned)ceil_div(p, PC), nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    LRA_LAUNCHED();
+}
+
 template <typename TX, int S, int NB, int D>
 void launch_batch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                   const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
@@ -592,22 +814,24 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
             LRA_PAIR_CASE(4, 2)
 #undef LRA_PAIR_CASE
         }
-#define LRA_INNER_CASE(SS, PCC)                                                                     \
-    if (S == SS && pc == PCC) {                                                                     \
-        launch_inner1<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);     \
-        return;                                                                                     \
+        // several warps: two steps per block barrier (look-ahead identity); the
+        // three column buffers of that kernel leave room for two columns per
+        // CTA only up to two row groups per thread
+        const int pcl = (p <= 64 || S > 2) ? 1 : 2;
+#define LRA_LA_CASE(SS, PCC)                                                                    \
+    if (S == SS && pcl == PCC) {                                                                \
+        launch_la<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);     \
+        return;                                                                                 \
     }
-        LRA_INNER_CASE(1, 1)
-        LRA_INNER_CASE(1, 2)
-        LRA_INNER_CASE(2, 1)
-        LRA_INNER_CASE(2, 2)
-        LRA_INNER_CASE(3, 1)
-        LRA_INNER_CASE(3, 2)
-        LRA_INNER_CASE(4, 1)
-        LRA_INNER_CASE(4, 2)
-        LRA_INNER_CASE(6, 1)
-        LRA_INNER_CASE(8, 1)
-#undef LRA_INNER_CASE
+        LRA_LA_CASE(1, 1)
+        LRA_LA_CASE(1, 2)
+        LRA_LA_CASE(2, 1)
+        LRA_LA_CASE(2, 2)
+        LRA_LA_CASE(3, 1)
+        LRA_LA_CASE(4, 1)
+#undef LRA_LA_CASE
+        // d > 8192: the look-ahead kernel's three column buffers would spill;
+        // one barrier per step
         if (S <= 6) {
             launch_inner1<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
         } else {

@@ -68,10 +68,12 @@ void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh
 // Y = X^T W on tcgen05: writes Y32 (n x PP row-major) and/or Yb (hi/lo) when
 // non-null.  X is BF16 (Xl == nullptr) or the BF16 pair (X, Xl) of an FP32 X.
 void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err);
+            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err,
+            long long wait_cycles = 0);
 // partial G = X Y per column chunk on tcgen05 (same Gp layout as xy)
 void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err);
+           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err,
+           long long wait_cycles = 0);
 
 // ---- SVRG inner loop (k_inner.cu) -----------------------------------------
 // m steps of `batch` samples each (idx, cval: m * batch entries); batch a power of two <= 16

@@ -15,7 +15,10 @@ namespace tc {
 enum : int { kErrTimeout = 1 };
 
 // A wait that has not completed after this many SM cycles gives up (about
-// 2 s at 2 GHz): the kernel records kErrTimeout and unwinds.
+// 2 s at 2 GHz): the kernel records kErrTimeout and unwinds.  The pipeline
+// waits take their limit as a kernel argument (this value by default); the
+// waits of the unwinding itself (copies and MMAs already issued) always use
+// this one.
 constexpr long long kWaitCycles = 4000000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -48,13 +51,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of `bar` with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase of `bar` with the given parity; false when it
+// has not completed after `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kWaitCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
