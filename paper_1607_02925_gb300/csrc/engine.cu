@@ -329,7 +329,7 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo)
     if (mat_->sp) {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
         if (timer) timer->begin(KernelTimer::XTW, p);
-        spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, ws_.Wr, PP, p, Y);
+        spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, mat_->d, ws_.Wr, PP, p, Y);
         if (timer) timer->end();
     } else if (tc(use32)) {
         pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);

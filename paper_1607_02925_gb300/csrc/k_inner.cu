@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <cstdlib>
 #include <string>
 
 #include "kernels.cuh"
@@ -347,28 +348,73 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
 //   r_{t+1} = a x_{t+1}^T Delta_t + c_t x_{t+1}^T x_t - x_{t+1}^T (eta M),
 // lets the dot products of steps t + 1 and t + 2 (the latter taken on
 // Delta_{t+1} once c_t is known, less its c_{t+1} term) share one block
-// reduction.  Each warp reduces its partial sums by shuffles; lane 0 writes
-// them to a shared row of 16 per value (zero for absent warps), and every
-// thread sums the 16 in a fixed order from four 16-byte loads.  Thread t owns
-// rows 4 (t + s NT) + v; the ring holds R columns, fetched R - 1 steps ahead,
-// and each thread copies and reads only its own rows of them.
-template <int N>
-__device__ __forceinline__ void block_sum16(float (&v)[N], float (*red)[16], int lane, int warp) {
+// reduction.  The kernel is bound by instruction issue, so it is written to
+// issue few: the per-thread dot products and the updates of Delta run on
+// packed FP32x2 FMAs (fma.rn.f32x2: two independent round-to-nearest FMAs,
+// the same values as two fmaf), a warp reduces its NV partial sums with a
+// transposing butterfly (NP/2 + NP/4 + ... exchanges instead of 5 per value),
+// and the NV totals are then summed over the warps from a shared row of 16
+// (zero for absent warps).  Thread t owns rows 4 (t + s NT) + v; the ring
+// holds R columns, fetched R - 1 steps ahead, and each thread copies and reads
+// only its own rows of them.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)),
+          "l"(*reinterpret_cast<const uint64_t *>(&c)));
+    return *reinterpret_cast<float2 *>(&d);
+}
+
+// Warp sums of NP values (NP a power of two, 2 <= NP <= 32): after the call
+// lane l holds the warp total of value l >> (5 - log2 NP).  Level o = 16, 8, ...
+// halves the values a lane keeps (the upper lanes keep the upper half) while
+// adding the partner's copy; the last levels add within each group of 32 / NP
+// lanes.  Fixed order, so the result does not depend on timing.
+template <int NP>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[NP], int lane) {
+    int cnt = NP;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = 16; o >= 32 / NP; o >>= 1) {
+        const int half = cnt >> 1;
+        const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) red[i][warp] = v[i];
+        for (int i = 0; i < NP / 2; ++i) {
+            if (i < half) {
+                const float send = upper ? v[i] : v[i + half];
+                const float keep = upper ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        cnt = half;
     }
+    float r = v[0];
+#pragma unroll
+    for (int o = 16 / NP; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// Block totals of NV values over NW <= 16 warps: warp totals by the
+// transposing butterfly, one shared row of 16 per value, every thread sums the
+// warps' entries in a fixed order from NW / 4 16-byte loads (entries of absent
+// warps hold zeros).
+template <int NV, int NP, int NW>
+__device__ __forceinline__ void block_sum16(float (&v)[NP], float (*red)[16], int lane, int warp) {
+    constexpr int LB = 5 - (NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : NP == 16 ? 4 : 5);
+    const float w = warp_transpose_sum<NP>(v, lane);
+    const int idx = lane >> LB;
+    if ((lane & ((1 << LB) - 1)) == 0 && idx < NV) red[idx][warp] = w;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < NV; ++i) {
         const float4 *q = reinterpret_cast<const float4 *>(red[i]);
-        const float4 a = q[0], b = q[1], c = q[2], d = q[3];
-        v[i] = (((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w))) +
-               (((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w)));
+        const float4 a = q[0], b = q[1];
+        float t = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
+        if constexpr (NW > 8) {
+            const float4 c = q[2], d = q[3];
+            t = t + (((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w)));
+        }
+        v[i] = t;
     }
 }
 
@@ -380,12 +426,16 @@ __host__ __device__ constexpr int la_ring() {
     return 8 * col <= 220 * 1024 ? 8 : 6 * col <= 220 * 1024 ? 6 : 4 * col <= 220 * 1024 ? 4 : 3;
 }
 
-template <typename TX, int S, int PC, int R = la_ring<TX, S>()>
+template <int NV>
+__host__ __device__ constexpr int pow2_at_least() { return NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32; }
+
+template <typename TX, int S, int PC, int NW, int R = la_ring<TX, S>()>
 __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
     const float *__restrict__ cval, int64_t m, float eta, float lam) {
     constexpr int NV = 4 * PC + 2;  // uA, wA, uB, wB per column, then vA, vB
+    constexpr int NP = pow2_at_least<NV>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TX *ring = reinterpret_cast<TX *>(smem_raw);  // [R][dpad]
     __shared__ __align__(16) float red[3][NV][16];
@@ -398,8 +448,9 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
 
     for (int e = tid; e < 3 * NV * 16; e += NT) (&red[0][0][0])[e] = 0.0f;
 
-    float dl[S][4][PC];   // Delta = W - Wt
-    float mm[S][4][PC];   // eta * M
+    // Delta = W - Wt and eta M, rows 4 (t + s NT) + {0, 1} and + {2, 3} as pairs
+    float2 dl[S][2][PC];
+    float2 mm[S][2][PC];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
@@ -408,9 +459,10 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
             const bool ok = (r < dpad) && (j0 + j < p);
             const int64_t off = r + (int64_t)(j0 + j) * dpad;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                dl[s][v][j] = ok ? (W[off + v] - Wt[off + v]) : 0.0f;
-                mm[s][v][j] = ok ? eta * M[off + v] : 0.0f;
+            for (int h = 0; h < 2; ++h) {
+                dl[s][h][j] = ok ? make_float2(W[off + 2 * h] - Wt[off + 2 * h], W[off + 2 * h + 1] - Wt[off + 2 * h + 1])
+                                 : make_float2(0.0f, 0.0f);
+                mm[s][h][j] = ok ? make_float2(eta * M[off + 2 * h], eta * M[off + 2 * h + 1]) : make_float2(0.0f, 0.0f);
             }
         }
     }
@@ -427,7 +479,7 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
         }
         cp_async_commit();
     };
-    auto load = [&](int64_t t, float (&x)[S][4]) {
+    auto load = [&](int64_t t, float2 (&x)[S][2]) {
         const TX *slot = ring + (t % R) * dpad;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -435,69 +487,77 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
             if (t < m && r < dpad) {
                 if constexpr (sizeof(TX) == 4) {
                     const float4 q = *reinterpret_cast<const float4 *>(slot + r);
-                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
+                    x[s][0] = make_float2(q.x, q.y);
+                    x[s][1] = make_float2(q.z, q.w);
                 } else {
                     const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
+                    const __nv_bfloat162 *e = reinterpret_cast<const __nv_bfloat162 *>(&q);
+                    x[s][0] = __bfloat1622float2(e[0]);
+                    x[s][1] = __bfloat1622float2(e[1]);
                 }
             } else {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
+                x[s][0] = make_float2(0.0f, 0.0f);
+                x[s][1] = make_float2(0.0f, 0.0f);
             }
         }
     };
     // partial sums of y^T Delta and y^T (eta M) per column, and y^T z
-    auto dots = [&](const float (&y)[S][4], const float (&z)[S][4], float *u, float *w, float &vv) {
+    auto dots = [&](const float2 (&y)[S][2], const float2 (&z)[S][2], float *u, float *w, float &vv) {
 #pragma unroll
         for (int j = 0; j < PC; ++j) {
-            float a0 = 0.0f, a1 = 0.0f;
+            float2 a0 = make_float2(0.0f, 0.0f), a1 = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    a0 = fmaf(y[s][v], dl[s][v][j], a0);
-                    a1 = fmaf(y[s][v], mm[s][v][j], a1);
+                for (int h = 0; h < 2; ++h) {
+                    a0 = ffma2(y[s][h], dl[s][h][j], a0);
+                    a1 = ffma2(y[s][h], mm[s][h][j], a1);
                 }
-            u[j] = a0;
-            w[j] = a1;
+            u[j] = a0.x + a0.y;
+            w[j] = a1.x + a1.y;
         }
-        float a2 = 0.0f;
+        float2 a2 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) a2 = fmaf(y[s][v], z[s][v], a2);
-        vv = a2;
+            for (int h = 0; h < 2; ++h) a2 = ffma2(y[s][h], z[s][h], a2);
+        vv = a2.x + a2.y;
     };
-    auto update = [&](const float (&x)[S][4], const float (&c)[PC], float a) {
+    const float a = 1.0f - eta * lam;
+    const float2 a2v = make_float2(a, a);
+    auto update = [&](const float2 (&x)[S][2], const float (&c)[PC]) {
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int j = 0; j < PC; ++j) dl[s][v][j] = fmaf(a, dl[s][v][j], fmaf(c[j], x[s][v], -mm[s][v][j]));
+                for (int j = 0; j < PC; ++j) {
+                    const float2 nm = make_float2(-mm[s][h][j].x, -mm[s][h][j].y);
+                    dl[s][h][j] = ffma2(a2v, dl[s][h][j], ffma2(make_float2(c[j], c[j]), x[s][h], nm));
+                }
     };
 
 #pragma unroll
     for (int u = 0; u < R - 1; ++u) prefetch(u);
-    const float a = 1.0f - eta * lam;
-    float x0[S][4], x1[S][4], x2[S][4];
+    float2 x0[S][2], x1[S][2], x2[S][2];
     float r[PC];
     cp_async_wait<R - 2>();
     load(0, x0);
     {
-        float v0[PC];
+        constexpr int NP0 = pow2_at_least<PC>();
+        float v0[NP0];
+#pragma unroll
+        for (int i = 0; i < NP0; ++i) v0[i] = 0.0f;
 #pragma unroll
         for (int j = 0; j < PC; ++j) {
-            float acc = 0.0f;
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int s = 0; s < S; ++s)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc = fmaf(x0[s][v], dl[s][v][j], acc);
-            v0[j] = acc;
+                for (int h = 0; h < 2; ++h) acc = ffma2(x0[s][h], dl[s][h][j], acc);
+            v0[j] = acc.x + acc.y;
         }
-        block_sum16<PC>(v0, red[2], lane, warp);
+        block_sum16<PC, NP0, NW>(v0, red[2], lane, warp);
 #pragma unroll
         for (int j = 0; j < PC; ++j) r[j] = v0[j];
     }
@@ -513,20 +573,22 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
         float ct[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
-        float acc[NV];
+        float acc[NP];
+#pragma unroll
+        for (int i = NV; i < NP; ++i) acc[i] = 0.0f;
         // chain A: r_{t+1} from Delta_t
         dots(x1, x0, acc, acc + PC, acc[4 * PC]);
         // step t
-        update(x0, ct, a);
+        update(x0, ct);
         // chain B: r_{t+2} from Delta_{t+1}, less the c_{t+1} term
         dots(x2, x1, acc + 2 * PC, acc + 3 * PC, acc[4 * PC + 1]);
-        block_sum16<NV>(acc, red[buf], lane, warp);
+        block_sum16<NV, NP, NW>(acc, red[buf], lane, warp);
         float c1[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) c1[j] = c1v * fmaf(a, acc[j], fmaf(ct[j], acc[4 * PC], -acc[PC + j]));
         if (t + 1 < m) {
             // step t + 1
-            update(x1, c1, a);
+            update(x1, c1);
 #pragma unroll
             for (int j = 0; j < PC; ++j)
                 r[j] = fmaf(a, acc[2 * PC + j], fmaf(c1[j], acc[4 * PC + 1], -acc[3 * PC + j]));
@@ -534,7 +596,7 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) x0[s][v] = x2[s][v];
+            for (int h = 0; h < 2; ++h) x0[s][h] = x2[s][h];
     }
     cp_async_wait<0>();
 
@@ -546,7 +608,10 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
             if (r0 < dpad && j0 + j < p) {
                 const int64_t off = r0 + (int64_t)(j0 + j) * dpad;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) W[off + v] = Wt[off + v] + dl[s][v][j];
+                for (int h = 0; h < 2; ++h) {
+                    W[off + 2 * h] = Wt[off + 2 * h] + dl[s][h][j].x;
+                    W[off + 2 * h + 1] = Wt[off + 2 * h + 1] + dl[s][h][j].y;
+                }
             }
         }
     }
@@ -738,11 +803,16 @@ template <typename TX, int S, int PC>
 void launch_la(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W, const float *Wt,
                const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam, int nt) {
     constexpr int R = la_ring<TX, S>();
-    auto k = svrg_inner_la_kernel<TX, S, PC, R>;
     const size_t smem = (size_t)R * dpad * sizeof(TX);
-    ensure_smem(k, (int)smem);
-    k<<<(unsigned)ceil_div(p, PC), nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
-    LRA_LAUNCHED();
+    auto go = [&](auto k) {
+        ensure_smem(k, (int)smem);
+        k<<<(unsigned)ceil_div(p, PC), nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+        LRA_LAUNCHED();
+    };
+    if (nt <= 256)
+        go(svrg_inner_la_kernel<TX, S, PC, 8, R>);
+    else
+        go(svrg_inner_la_kernel<TX, S, PC, 16, R>);
 }
 
 template <typename TX, int S, int NB, int D>
@@ -817,6 +887,14 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
         // several warps: two steps per block barrier (look-ahead identity); the
         // three column buffers of that kernel leave room for two columns per
         // CTA only up to two row groups per thread
+        // the kernel is bound by instruction issue: 8 warps (four row groups
+        // per thread) up to d = 4096 issue fewer reduction instructions per step
+        // than 16 (measured 594 against 716 ns per step at d = 4096, p = 40);
+        // beyond, the register state of four groups caps the threads at 512
+        if (groups > 256 && groups <= 1024) {
+            nt = 256;
+            S = ceil_div(groups, nt);
+        }
         const int pcl = (p <= 64 || S > 2) ? 1 : 2;
 #define LRA_LA_CASE(SS, PCC)                                                                    \
     if (S == SS && pcl == PCC) {                                                                \

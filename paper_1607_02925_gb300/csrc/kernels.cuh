@@ -161,7 +161,7 @@ void sparse_fill_items(cudaStream_t s, const int64_t *item_off, int64_t dpad, in
 void sparse_colnorms(cudaStream_t s, const int64_t *colptr, const float *cval, int64_t n, double *norm2);
 // Y (n x PP row-major) = X^T Wr (Wr dpad x PP row-major, columns >= p zero)
 void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t n,
-             const float *Wr, int PP, int p, float *Y);
+             int64_t d, const float *Wr, int PP, int p, float *Y);
 // G (dpad x PP row-major) = X Y (Y columns >= p zero); partial >= nitems x PP floats
 void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
             int64_t dpad, const int64_t *item_off, const int2 *items, int64_t nitems, int seg, const float *Y,

@@ -33,8 +33,15 @@ def elem_bound(a, b, scale) -> float:
 
 
 def elem_rms(a, b) -> float:
-    """max |a - b| / (|b| + rms(b)), elementwise."""
+    """max |a - b| / (|b| + rms(b)) over the N elements, divided by
+    sqrt(2 ln N): independent rounding errors of relative size t (Frobenius)
+    reach about t sqrt(2 ln N) at their largest element, so this measure is
+    about t for them, while a localized error (a wrong tile or row) keeps its
+    full size."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    rms = float(np.sqrt(np.mean(b * b))) if b.size else 0.0
-    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b) + rms, 1e-300))) if b.size else 0.0
+    if not b.size:
+        return 0.0
+    rms = float(np.sqrt(np.mean(b * b)))
+    worst = float(np.max(np.abs(a - b) / np.maximum(np.abs(b) + rms, 1e-300)))
+    return worst / np.sqrt(2.0 * np.log(max(b.size, 3)))
