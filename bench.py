@@ -48,7 +48,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lra", "reference"], default="lra")
     ap.add_argument("--workload", default="exp_two_gaps_8192x1048576")
-    ap.add_argument("--storage", choices=["f32", "bf16"], default="bf16")
+    ap.add_argument("--storage", choices=["f32", "bf16"], default=None,
+                    help="storage of a dense X (default: the workload's own: BF16 for exp_two_gaps, else FP32)")
     ap.add_argument("--companion", choices=["auto", "none", "f32", "bf16"], default="auto",
                     help="the same matrix in the other storage type, timed beside the headline "
                          "(auto: FP32 for a BF16 headline on a dense workload)")
@@ -332,8 +333,9 @@ class DenseSource:
         torch.cuda.empty_cache()
         return tot - proj
 
-    def pass_bytes(self, kind, pav):
-        return self.x_bytes + (self.wl.d + self.wl.n) * pav * 4
+    def pass_bytes(self, kind, pav, storage=None):
+        esize = self.esize if storage is None else (4 if storage == "f32" else 2)
+        return self.wl.d * self.wl.n * esize + (self.wl.d + self.wl.n) * pav * 4
 
     def oracle_input(self, cols=None):
         """The host copy of X (its first `cols` columns when X is sampled)."""
@@ -401,7 +403,7 @@ class CsrSource:
         v = self.val.astype(np.float64)
         return float(np.sum(v * v)) - float(np.sum(P * P))
 
-    def pass_bytes(self, kind, pav):
+    def pass_bytes(self, kind, pav, storage=None):
         wl = self.wl
         # compressed index + value of every non-zero, the line pointers, the
         # dense operand and the result (gathers of the operand hit L2)
@@ -520,7 +522,7 @@ def kernel_table(reps, src, storage, wl, peaks, peak_kind, workload):
             e = {"launches": cnt[kk], "ms_total": tot[kk], "ms_per_launch": tot[kk] / cnt[kk]}
             if kk in cols:
                 pav = cols[kk] / cnt[kk]
-                e["x_pass_gbs"] = src.pass_bytes(kk, pav) / (tot[kk] / cnt[kk] / 1e3) / 1e9
+                e["x_pass_gbs"] = src.pass_bytes(kk, pav, storage) / (tot[kk] / cnt[kk] / 1e3) / 1e9
                 e["frac_of_hbm"] = e["x_pass_gbs"] / peaks["hbm_gbs"]
             if kk == "inner":
                 steps = sum(r.inner_steps for _, r in reps)
@@ -535,7 +537,7 @@ def kernel_table(reps, src, storage, wl, peaks, peak_kind, workload):
     roof = None
     if dom in ("xtw", "xy") and cnt[dom] > 0:
         pav = cols[dom] / cnt[dom]
-        bytes_l = src.pass_bytes(dom, pav)
+        bytes_l = src.pass_bytes(dom, pav, storage)
         t_l = tot[dom] / cnt[dom] / 1e3
         hbm = peaks["hbm_gbs"] * 1e9
         compute_bound = False
@@ -896,6 +898,8 @@ def run_serve(args):
 
 def main():
     args = parse_args()
+    if args.storage is None:
+        args.storage = "bf16" if L.WORKLOADS[args.workload].storage == "bf16" else "f32"
     if args.serve:
         return run_serve(args)
     if args.impl == "reference":
