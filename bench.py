@@ -48,11 +48,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lra", "reference"], default="lra")
     ap.add_argument("--workload", default="exp_two_gaps_8192x1048576")
-    ap.add_argument("--storage", choices=["f32", "bf16"], default=None,
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default=None,
                     help="storage of a dense X (default: the workload's own: BF16 for exp_two_gaps, else FP32)")
-    ap.add_argument("--companion", choices=["auto", "none", "f32", "bf16"], default="auto",
-                    help="the same matrix in the other storage type, timed beside the headline "
-                         "(auto: FP32 for a BF16 headline on a dense workload)")
+    ap.add_argument("--companion", default="auto",
+                    help="comma-separated storage types (f32, bf16, f16) of the same matrix timed beside the "
+                         "headline; auto: f32,f16 for a BF16 headline on a dense workload; none")
     ap.add_argument("--companion-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true", help="leave out the embedded request-loop benchmark")
@@ -224,7 +224,7 @@ def oracle_sample(wl, Xt_host, args, lam1_hat, outer_sample, threads):
     lh = O.lambda1_estimate(ctx)
     t_fixed = time.perf_counter() - t0
     o = O.Options(shift_policy=pol, delta=delta, min_outer=outer_sample, max_outer=outer_sample,
-                  tau=1e-3 if args.storage == "bf16" else 1e-5, batch=args.batch,
+                  tau={"bf16": 1e-3, "f16": 1e-4}.get(args.storage, 1e-5), batch=args.batch,
                   acc=int(args.acc), acc_target=args.acc_target)
     t0 = time.perf_counter()
     r = O.solve(X64, wl.k, wl.p, args.eps, args.seed, o, lam1_hat=lh)
@@ -239,7 +239,7 @@ def oracle_partition(wl, Xt_host, args, delta, threads):
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     from oracle import lra_oracle as O
     from oracle import lra_partition as P
-    o = O.Options(tau=1e-3 if args.storage == "bf16" else 1e-5, batch=args.batch, acc=int(args.acc),
+    o = O.Options(tau={"bf16": 1e-3, "f16": 1e-4}.get(args.storage, 1e-5), batch=args.batch, acc=int(args.acc),
                   acc_target=args.acc_target)
     t0 = time.perf_counter()
     P.adaptive_solve(O.as64(Xt_host), wl.k, wl.p, args.eps, args.seed, o, delta=delta)
@@ -290,7 +290,7 @@ class DenseSource:
     def __init__(self, args, wl, device, lra):
         import torch
         self.wl, self.lra, self.args = wl, lra, args
-        self.storage = lra.LRA_F32 if args.storage == "f32" else lra.LRA_BF16
+        self.storage = {"f32": lra.LRA_F32, "bf16": lra.LRA_BF16, "f16": lra.LRA_F16}[args.storage]
         self.esize = 4 if args.storage == "f32" else 2
         self.Xt, _ = L.planted_torch(wl.d, wl.n, wl.sigma(), wl.seed, device=device)
         torch.cuda.synchronize()
@@ -546,7 +546,7 @@ def kernel_table(reps, src, storage, wl, peaks, peak_kind, workload):
             # k-step (hi/lo small operand), FP32 X as a BF16 pair with 3; the
             # executed tensor flops are compared with the measured sustained BF16 peak
             flops_l = 2.0 * wl.d * wl.n * pav
-            mmas = 2 if storage == "bf16" else 3
+            mmas = 3 if storage == "f32" else 2
             tens = peaks["bf16_tflops_sustained"] * 1e12 / mmas
             compute_bound = bytes_l / hbm < flops_l / tens
         if compute_bound:
@@ -613,21 +613,26 @@ def run_lra(args):
     mat = None
     torch.cuda.empty_cache()
 
-    # ---- companion: the same matrix, seed and eps in the other storage type
-    comp_storage = args.companion
-    if comp_storage == "auto":
-        comp_storage = "f32" if (wl.storage != "csr" and args.storage == "bf16") else "none"
-    companion = None
-    if comp_storage != "none" and wl.storage != "csr" and args.companion_steps > 0:
-        cst = lra.LRA_F32 if comp_storage == "f32" else lra.LRA_BF16
+    # ---- companions: the same matrix, seed and eps in other storage types
+    comps = args.companion
+    if comps == "auto":
+        comps = "f32,f16" if (wl.storage != "csr" and args.storage == "bf16") else "none"
+    companions = {}
+    for comp_storage in ([] if comps == "none" or wl.storage == "csr" or args.companion_steps <= 0
+                         else comps.split(",")):
+        cst = {"f32": lra.LRA_F32, "bf16": lra.LRA_BF16, "f16": lra.LRA_F16}[comp_storage]
+        copt = lra.options(shift_policy=pol, delta=delta, profile=1, batch=args.batch, acc=int(args.acc),
+                           acc_target=args.acc_target, partition=int(args.partition))
+        if args.max_outer > 0:
+            copt.max_outer = args.max_outer
         m2 = lra.lra_create_dense(ctx, wl.d, wl.n, lra.LRA_F32, src.Xt, wl.d, True, cst)
-        ms2, reps2, U2 = timed_solves(lra, m2, wl, args, opt, stream, args.companion_steps, 1)
+        ms2, reps2, U2 = timed_solves(lra, m2, wl, args, copt, stream, args.companion_steps, 1)
         if world > 1:
             ms2 = max_over_ranks(ms2, device)
         lra.lra_mat_destroy(m2)
         torch.cuda.empty_cache()
         roof2, pk2, _ = kernel_table(reps2, src, comp_storage, wl, peaks, peak_kind, args.workload)
-        companion = {
+        companions[comp_storage + "_companion"] = {
             "storage": comp_storage, "time_to_eps_s": ms2 / 1e3, "steps": args.companion_steps, "warmup": 1,
             "ratio_err_over_opt": src.err(U2) / opt_val, "outer_iters": reps2[-1][1].outer_iters,
             "status": reps2[-1][0],
@@ -708,7 +713,7 @@ def run_lra(args):
             "phases_ms": {name: sum(r.phase_ms[i] for _, r in reps) / args.steps
                           for i, name in enumerate(["xtw", "xy", "inner", "ritz_gram", "eig", "cholqr2",
                                                     "warm_start", "epilogue"])},
-            "f32_companion" if comp_storage == "f32" else "companion": companion,
+            **companions,
             "serve": serve,
             "cpu_baseline": cpu,
         }

@@ -81,7 +81,7 @@ typedef struct lra_options {
     double delta;           /* gap budget Delta <= lambda_k - lambda_{p+1} <= 2 Delta (Sec. 3); 0 = estimate */
     double theta_eta;       /* step size eta = theta_eta mu / (lambda^2 + kappa lambda1_up); default 0.25 */
     double theta_m;         /* epoch length m = ceil(theta_m / (eta mu)); default 2 */
-    double tau;             /* SVRG stop: ||M||_F <= tau ||B||_F; 0 = 1e-5 (FP32 X) / 1e-3 (BF16 X) */
+    double tau;             /* SVRG stop: ||M||_F <= tau ||B||_F; 0 = 1e-5 (FP32 X), 1e-4 (FP16 X), 1e-3 (BF16 X) */
     int max_epochs;         /* anchors per solve; default 60 */
     int64_t m_max;          /* cap on m; 0 = 50 n */
     int min_outer;          /* outer iterations before the stop rule may fire; default 3 */
@@ -195,9 +195,18 @@ lra_status lra_finalize(lra_ctx *ctx);
 
 /* Copy a dense X (d x n, column-major, leading dimension ld >= d) of type `src`
  * from host or device memory (src_on_device = 0/1) into library-owned device
- * storage of type `storage` (LRA_F32 or LRA_BF16; BF16 is round-to-nearest-even).
- * A BF16-stored matrix also keeps an FP32 copy for the final Rayleigh-Ritz
- * step.  The caller may free X on return.  Requires 1 <= d, 2 <= n. */
+ * storage of type `storage`, the element type the X passes of Sec. 2.3 stream
+ * (conversions round to nearest even):
+ *   LRA_F32  - FP32; the tensor-core passes stream it as a BF16 hi/lo pair;
+ *   LRA_BF16 - BF16 (2 bytes per entry streamed);
+ *   LRA_F16  - FP16 (2 bytes per entry streamed, 3 more significand bits than
+ *              BF16): X is stored as fp16(s x) with s the power of two that
+ *              puts max |x| in [2^14, 2^15), so entries far below FP16's
+ *              normal range keep their precision; every pass divides s out
+ *              again (exactly), so all entry points see X itself.
+ * A BF16- or FP16-stored matrix also keeps an FP32 copy for the final
+ * Rayleigh-Ritz step.  The caller may free X on return.  Requires 1 <= d,
+ * 2 <= n. */
 lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, const void *X,
                             int64_t ld, int src_on_device, lra_dtype storage, lra_mat **out);
 

@@ -217,8 +217,8 @@ lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, c
         set_error("source dtype must be F32, BF16 or F64");
         return LRA_EUNSUPPORTED;
     }
-    if (storage != LRA_F32 && storage != LRA_BF16) {
-        set_error("storage dtype must be F32 or BF16");
+    if (storage != LRA_F32 && storage != LRA_BF16 && storage != LRA_F16) {
+        set_error("storage dtype must be F32, BF16 or F16");
         return LRA_EUNSUPPORTED;
     }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -236,7 +236,7 @@ lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, c
         const size_t ncell = (size_t)m->dpad * n;
         try {
             m->X32 = static_cast<float *>(dev_alloc(ctx, sizeof(float) * ncell));
-            if (storage == LRA_BF16) m->X = dev_alloc(ctx, sizeof(__nv_bfloat16) * ncell);
+            if (storage == LRA_BF16 || storage == LRA_F16) m->X = dev_alloc(ctx, sizeof(__nv_bfloat16) * ncell);
             else m->X = m->X32;
             const size_t es = dtype_size(src);
             const cudaStream_t s = ctx->stream;
@@ -262,6 +262,19 @@ lra_status lra_create_dense(lra_ctx *ctx, int64_t d, int64_t n, lra_dtype src, c
                                     static_cast<__nv_bfloat16 *>(m->X) + (size_t)c0 * m->dpad, m->dpad);
                 }
                 if (!dev) LRA_CUDA(cudaStreamSynchronize(s));
+            }
+            if (storage == LRA_F16) {
+                // FP16 storage: fp16(xscale x), xscale a power of two that puts
+                // max |x| in [2^14, 2^15) (the FP32 copy keeps the exact values)
+                unsigned *word = static_cast<unsigned *>(dev_alloc(ctx, sizeof(unsigned)));
+                try {
+                    m->xscale = f16_storage_scale(s, m->X32, (int64_t)ncell, word);
+                } catch (...) {
+                    dev_free(ctx, word, sizeof(unsigned));
+                    throw;
+                }
+                dev_free(ctx, word, sizeof(unsigned));
+                to_f16(s, m->X32, (int64_t)ncell, m->xscale, static_cast<__half *>(m->X));
             }
             if (storage == LRA_F32) {
                 // the tensor-core passes stream the FP32 values as a BF16 pair

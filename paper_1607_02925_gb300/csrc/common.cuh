@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -85,6 +86,22 @@ __host__ __device__ __forceinline__ uint64_t stream_word(uint64_t key, uint64_t 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// Four consecutive elements (16-byte aligned for float, 8-byte for the 16-bit
+// types) widened to FP32.
+template <typename TX>
+__device__ __forceinline__ void load4_f32(const TX *p, float (&x)[4]) {
+    if constexpr (sizeof(TX) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+    } else {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const TX *e = reinterpret_cast<const TX *>(&q);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = to_f32(e[v]);
+    }
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -76,7 +76,7 @@ Opts read_opts(const lra_options *o, lra_dtype storage) {
         r.part_max_iters = o->part_max_iters;
         r.wait_cycles = o->wait_cycles;
     }
-    if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : 1e-5;
+    if (r.tau <= 0.0) r.tau = (storage == LRA_BF16) ? 1e-3 : (storage == LRA_F16 ? 1e-4 : 1e-5);
     if (r.shift_policy < 0 || r.shift_policy > 2 || r.theta_eta <= 0 || r.theta_m <= 0 ||
         r.max_epochs < 1 || r.max_outer < 0 || r.sampling < 0 || r.sampling > 1 || r.fixed_epochs < 0 ||
         r.max_shift_rounds < 1 || r.m_max < 0 || !(r.delta >= 0.0) || r.batch < 1 || r.batch > 16 ||
@@ -101,6 +101,7 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
     b += sizeof(double) * (9 * pmax * pmax + gram_scratch(pmax) + dpad);
+    b += sizeof(float) * (2 + 2 * (size_t)PP);  // scales of FP16 tensor-core operands
     if (sp_items >= 0)
         b += sizeof(float) * (size_t)sp_items * PP;                 // partial
     else
@@ -155,6 +156,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         status = alloc<int>(4);
         tcerr = alloc<int>(4);
         zero(tcerr, sizeof(int) * 4);
+        tcs = alloc<float>(2 + 2 * (size_t)PPmax);
         if (sp_items >= 0) {
             partial = alloc<float>((size_t)std::max<int64_t>(sp_items, 1) * PPmax);
         } else {
@@ -264,7 +266,7 @@ void Engine::ensure_norms() {
     if (mat_->sp)
         sparse_colnorms(s_, mat_->sp->colptr, mat_->sp->cval, mat_->n, mat_->norm2);
     else
-        colnorms(s_, mat_->X, mat_->storage, mat_->dpad, mat_->d, mat_->n, mat_->norm2);
+        colnorms(s_, mat_->X, mat_->storage, mat_->dpad, mat_->d, mat_->n, mat_->norm2, mat_->xscale);
     sum_max(s_, mat_->norm2, mat_->n, mat_->dev_sm, nullptr);
     double h[2];
     LRA_CUDA(cudaMemcpyAsync(h, mat_->dev_sm, sizeof(h), cudaMemcpyDeviceToHost, s_));
@@ -332,12 +334,19 @@ void Engine::xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo)
         spmm_xt(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->n, mat_->d, ws_.Wr, PP, p, Y);
         if (timer) timer->end();
     } else if (tc(use32)) {
-        pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
+        const bool f16 = mat_->storage == LRA_F16;
+        if (f16) {
+            ensure_norms();  // the bound max_i ||x_i|| behind the scales of Y's FP16 copy
+            pack_hilo_f16(s_, W, mat_->dpad, mat_->dpad, p, PP, mat_->xscale, std::sqrt(mat_->maxn), ws_.tcs,
+                          reinterpret_cast<__half *>(ws_.Wb));
+        } else {
+            pack_hilo(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wb);
+        }
         if (timer) timer->begin(KernelTimer::XTW, p);
-        // the BF16 hi/lo copy of Y feeds a following X Y pass; an FP32 result
+        // the 16-bit hi/lo copy of Y feeds a following X Y pass; an FP32 result
         // (Rayleigh-Ritz, the power steps) is used alone unless keep_hilo
         xtw_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Wb, PP, Y, (Y && !keep_hilo) ? nullptr : ws_.Yb,
-               ws_.ldy, ws_.tcerr, tc_wait_);
+               ws_.ldy, ws_.tcerr, tc_wait_, f16, ws_.tcs);
         if (timer) timer->end();
     } else {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
@@ -354,16 +363,28 @@ void Engine::xy_pass(const float *Y32, int p, bool use32) {
         const auto &sp = *mat_->sp;
         ws_.nch = 1;
         if (timer) timer->begin(KernelTimer::XY, p);
+        gscale_ = nullptr;
         spmm_x(s_, sp.rowptr, sp.colidx, sp.val, mat_->d, mat_->dpad, sp.item_off, sp.items, sp.nitems, kSparseSeg,
                Y32, PP, p, ws_.Gp, ws_.partial);
         if (timer) timer->end();
     } else if (tc(use32)) {
-        if (Y32) y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
+        const bool f16 = mat_->storage == LRA_F16;
+        if (Y32) {
+            if (f16)
+                y_hilo_f16(s_, Y32, mat_->n, PP, p, mat_->xscale, ws_.tcs, reinterpret_cast<__half *>(ws_.Yb),
+                           ws_.ldy);
+            else
+                y_hilo(s_, Y32, mat_->n, PP, ws_.Yb, ws_.ldy);
+        }
         ws_.nch = xy_chunks(mat_->dpad, mat_->n, tc_rows_per_cta(PP, mat_->Xl != nullptr));
         if (timer) timer->begin(KernelTimer::XY, p);
-        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp, ws_.nch, ws_.tcerr, tc_wait_);
+        xy_tc(s_, tcx(), mat_->Xl, mat_->dpad, mat_->n, ws_.Yb, ws_.ldy, PP, ws_.Gp, ws_.nch, ws_.tcerr, tc_wait_,
+              f16);
         if (timer) timer->end();
+        // FP16 operands: column c of the partials carries xscale sy_c
+        gscale_ = f16 ? ws_.tcs + 2 + PP : nullptr;
     } else {
+        gscale_ = nullptr;
         ws_.nch = xy_chunks(mat_->dpad, mat_->n, 128);
         if (timer) timer->begin(KernelTimer::XY, p);
         xy(s_, xptr(use32), xdt(use32), mat_->dpad, mat_->dpad, mat_->n, Y32, PP, ws_.Gp, ws_.nch);
@@ -375,7 +396,7 @@ void Engine::xy_pass(const float *Y32, int p, bool use32) {
 void Engine::x_mul(const float *Y, int p, float *G, bool use32) {
     xy_pass(Y, p, use32);
     anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
-                    ws_.epi);
+                    ws_.epi, nullptr, 0.0, gscale_);
 }
 
 void Engine::a_apply(const float *W, int p, float *G) {
@@ -387,7 +408,7 @@ void Engine::a_apply(const float *W, int p, float *G) {
         xy_pass(ws_.Y, p, false);
     }
     anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
-                    ws_.epi);
+                    ws_.epi, nullptr, 0.0, gscale_);
 }
 
 void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
@@ -408,7 +429,7 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
     if (!G0) nch = ws_.nch;
     if (timer) timer->begin(KernelTimer::EPI, p);
     anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi, acc ? acc->Z : nullptr,
-                    acc ? acc->gamma : 0.0);
+                    acc ? acc->gamma : 0.0, G0 ? nullptr : gscale_);
     if (timer) timer->end();
     if (nM2 || nB2) {
         LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, (acc ? 3 : 2) * sizeof(double), cudaMemcpyDeviceToHost, s_));
@@ -435,7 +456,7 @@ void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32
     }
     if (timer) timer->begin(KernelTimer::INNER, p);
     svrg_inner(s_, mat_->X, mat_->storage, mat_->dpad, mat_->dpad, p, W, Wt, M, idx, cval, m,
-               (float)eta, (float)lam, batch);
+               (float)eta, (float)lam, batch, 1.0f / (mat_->xscale * mat_->xscale));
     if (timer) timer->end();
 }
 

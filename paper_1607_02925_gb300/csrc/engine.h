@@ -36,6 +36,10 @@ struct lra_mat {
     // FP32 storage: BF16 pair (x = hi + lo + r, |r| <= 2^-17 |x|) streamed by the
     // tensor-core X passes; null for BF16 storage
     __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
+    // FP16 storage: X holds fp16(xscale x) with xscale a power of two that puts
+    // max |x| in [2^14, 2^15) (FP16's normal range starts at 2^-14); every pass
+    // over X divides it out again (the X passes, column norms, inner steps)
+    float xscale = 1.0f;
     // sparse X (X == nullptr): CSR of the d rows, compressed columns x_i, and
     // the row work list of X Y (item = (row, segment of kSparseSeg entries))
     struct Sparse {
@@ -160,6 +164,7 @@ struct Workspace {
     int64_t ldy = 0;
     int *status = nullptr;
     int *tcerr = nullptr;  // error word of the tensor-core kernels
+    float *tcs = nullptr;  // scales of the FP16 tensor-core operands (2 + 2 PPmax)
     int32_t *idx = nullptr;
     float *cval = nullptr;
     int64_t idx_cap = 0;
@@ -281,16 +286,15 @@ class Engine {
     Stats stats;
     KernelTimer *timer = nullptr;
     long long tc_wait_ = 0;  // pipeline wait limit of the tensor-core passes (0 = default)
+    const float *gscale_ = nullptr;  // per-column factor of the last X Y pass's partials (FP16 storage)
 
    private:
     // tensor-core passes: BF16 X, or the BF16 pair of an FP32 X; the exact FP32
     // values (use32) go through the CUDA-core kernels
     bool tc(bool use32) const {
-        return !use32 && !mat_->sp && (mat_->storage == LRA_BF16 || mat_->Xh != nullptr);
+        return !use32 && !mat_->sp && (mat_->storage == LRA_BF16 || mat_->storage == LRA_F16 || mat_->Xh != nullptr);
     }
-    const __nv_bfloat16 *tcx() const {
-        return mat_->Xh ? mat_->Xh : static_cast<const __nv_bfloat16 *>(mat_->X);
-    }
+    const void *tcx() const { return mat_->Xh ? static_cast<const void *>(mat_->Xh) : mat_->X; }
     // G-partials of one X Y pass into ws.Gp; Y32 == nullptr means ws.Yb already holds Y
     void xy_pass(const float *Y32, int p, bool use32);
     const void *xptr(bool use32) const { return use32 ? (const void *)mat_->X32 : mat_->X; }

@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__
                                                        const float *__restrict__ B,
                                                        const float *__restrict__ Z, double gamma,
                                                        float *__restrict__ out, int mode,
-                                                       double *__restrict__ partial) {
+                                                       double *__restrict__ partial,
+                                                       const float *__restrict__ colscale) {
     extern __shared__ __align__(16) float tile[];  // [kER][PP + 1]
     __shared__ double red[3][8];
     const int tid = threadIdx.x;
@@ -322,7 +323,9 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const float *__restrict__
             a3 += Gp[(c + 3) * stride + off];
         }
         for (; c < nchunks; ++c) a0 += Gp[c * stride + off];
-        tile[(e / PP) * ts + (e % PP)] = (a0 + a1) + (a2 + a3);
+        float g = (a0 + a1) + (a2 + a3);
+        if (colscale) g *= colscale[e % PP];  // a power of two: exact
+        tile[(e / PP) * ts + (e % PP)] = g;
     }
     __syncthreads();
     double m2 = 0.0, b2 = 0.0, r2 = 0.0;
@@ -478,11 +481,12 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
 
 void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
-                     double *scratch, const float *Z, double gamma) {
+                     double *scratch, const float *Z, double gamma, const float *colscale) {
     const int nb = (int)(dpad / kER);
     const size_t smem = sizeof(float) * kER * (PP + 1);
     const int mode = (Wt != nullptr) ? 0 : 1;
-    epilogue_kernel<<<nb, 256, smem, s>>>(Gp, nchunks, dpad, PP, p, lam, Wt, B, Z, gamma, M, mode, scratch);
+    epilogue_kernel<<<nb, 256, smem, s>>>(Gp, nchunks, dpad, PP, p, lam, Wt, B, Z, gamma, M, mode, scratch,
+                                          colscale);
     LRA_LAUNCHED();
     if (mode == 0 && norms) {
         norms_final_kernel<<<1, 32, 0, s>>>(scratch, nb, Z ? 3 : 2, norms);

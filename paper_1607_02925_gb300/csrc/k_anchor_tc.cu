@@ -9,6 +9,7 @@
 // FP32 small operand is split into BF16 hi + lo, both multiplied into the same
 // accumulator, so its rounding error is ~2^-17 instead of 2^-9.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -110,13 +111,19 @@ __device__ __forceinline__ void drain_mmas(Ctl *ctl) {
 // ---------------------------------------------------------------------------
 // Y = X^T W: work tile = MT x 128 data points (rows of X^T), K = d
 // ---------------------------------------------------------------------------
-template <int PP, int NA, int MT>
+// FMT = 1: BF16 operands.  FMT = 0: FP16 operands (FP16 storage): X holds
+// fp16(xscale x), the small operand fp16 hi / lo of w sw, and tcs holds the
+// scales: tcs[0] = sw, tcs[1] = 1 / (xscale sw), tcs[2 + c] = sy_c (the
+// multiplier of column c of Y in its FP16 hi / lo copy), tcs[2 + PP + c] =
+// 1 / (xscale sy_c).  All are powers of two, so the scaling is exact.
+template <int PP, int NA, int MT, int FMT>
 __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                                                              const __grid_constant__ CUtensorMap tmXl,
                                                              const __grid_constant__ CUtensorMap tmW,
                                                              int nkb, int64_t n, float *__restrict__ Y32,
-                                                             __nv_bfloat16 *__restrict__ Yb, int64_t ldy,
-                                                             int *__restrict__ err, long long lim) {
+                                                             uint16_t *__restrict__ Yb, int64_t ldy,
+                                                             int *__restrict__ err, long long lim,
+                                                             const float *__restrict__ tcs) {
     using T = Tile<PP, NA, MT>;
     constexpr int S = T::kStages;
     constexpr int KS = seg_kb<NA>();
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: the K blocks of a tile form segments of KS; segment sc
         // (counted over the CTA's whole walk) accumulates into set sc & 1
-        constexpr uint32_t idesc = instr_desc(1, 0, 0, PP, kBM);
+        constexpr uint32_t idesc = instr_desc(FMT, 0, 0, PP, kBM);
         int g = 0, sc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -219,8 +226,12 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
         const int q = warp & 3;
         int sc = 0;
         bool ok = true;
-        auto store = [&](int64_t i, int c, const float *v) {
+        const float ysc = FMT == 0 ? tcs[1] : 1.0f;
+        auto store = [&](int64_t i, int c, const float *v0) {
             if (i >= n) return;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = FMT == 0 ? v0[j] * ysc : v0[j];
             if (Y32) {
                 float4 *dst = reinterpret_cast<float4 *>(Y32 + i * PP + c);
 #pragma unroll
@@ -229,8 +240,17 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
             if (Yb) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                    uint16_t hi, lo;
+                    if constexpr (FMT == 0) {
+                        const float y = v[j] * tcs[2 + c + j];
+                        const __half h = __float2half_rn(y);
+                        hi = __half_as_ushort(h);
+                        lo = __half_as_ushort(__float2half_rn(y - __half2float(h)));
+                    } else {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+                        hi = __bfloat16_as_ushort(h);
+                        lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[j] - __bfloat162float(h)));
+                    }
                     Yb[(int64_t)(c + j) * ldy + i] = hi;
                     Yb[(int64_t)(PP + c + j) * ldy + i] = lo;
                 }
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) xtw_tc_kernel(const __grid_consta
 // Work tile = (MT x 128 rows of X, one column chunk); row tiles vary fastest,
 // so the CTAs in flight share the chunk's Y tiles in L2.
 // ---------------------------------------------------------------------------
-template <int PP, int NA, int MT>
+template <int PP, int NA, int MT, int FMT>
 __global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmXl,
                                                             const __grid_constant__ CUtensorMap tmY,
@@ -380,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) xy_tc_kernel(const __grid_constan
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: segments of KS K blocks; segment sc accumulates into set
         // sc & 1 (an empty chunk is one empty segment, drained as zeros)
-        constexpr uint32_t idesc = instr_desc(1, 1, 0, PP, kBM);
+        constexpr uint32_t idesc = instr_desc(FMT, 1, 0, PP, kBM);
         int g = 0, sc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -548,6 +568,105 @@ __global__ void split_hilo_kernel(const float *__restrict__ X, int64_t count, __
 }
 
 // Yb (hi/lo, column-major, leading dim ldy) from Y (n x PP row-major FP32)
+// FP16 operands (FP16 storage): scales from the block W (one CTA).  sw puts
+// max |w| in [2^13, 2^14); sy_c bounds column c of Y = X^T W through
+// |y_ic| <= ||x_i|| ||w_c|| <= sqrt(max_i ||x_i||^2) ||w_c|| and puts the bound
+// in [2^13, 2^14), so the FP16 hi / lo copy of Y never overflows and its
+// typical entries stay in FP16's normal range.
+__device__ __forceinline__ float pow2_below(float target, float v) {
+    // the largest power of two s with s v < target (1 for v = 0 or non-finite v)
+    if (!(v > 0.0f) || !isfinite(v)) return 1.0f;
+    int e = 0;
+    frexpf(target / v, &e);  // target / v in [2^(e-1), 2^e)
+    return ldexpf(1.0f, e - 1);
+}
+
+__global__ void __launch_bounds__(256) tc_scales_kernel(const float *__restrict__ W, int64_t ld, int64_t rows, int p,
+                                                        int PP, float xscale, float xmaxnorm,
+                                                        float *__restrict__ tcs) {
+    __shared__ float smax[256];
+    __shared__ double snorm[256];
+    float mx = 0.0f;
+    for (int64_t e = threadIdx.x; e < rows * p; e += 256) mx = fmaxf(mx, fabsf(W[(e % rows) + (e / rows) * ld]));
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float sw = pow2_below(16384.0f, smax[0]);
+        tcs[0] = sw;
+        tcs[1] = 1.0f / (xscale * sw);
+    }
+    for (int c = 0; c < PP; ++c) {
+        double a = 0.0;
+        if (c < p)
+            for (int64_t r = threadIdx.x; r < rows; r += 256) {
+                const double w = W[r + (int64_t)c * ld];
+                a += w * w;
+            }
+        snorm[threadIdx.x] = a;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) snorm[threadIdx.x] += snorm[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const float sy = pow2_below(16384.0f, xmaxnorm * (float)sqrt(snorm[0]));
+            tcs[2 + c] = sy;
+            tcs[2 + PP + c] = 1.0f / (xscale * sy);
+        }
+        __syncthreads();
+    }
+}
+
+// Wb[j][r] = hi / Wb[PP + j][r] = lo of sw W[r + j ld] in FP16 (zero for j >= p)
+__global__ void pack_hilo_f16_kernel(const float *__restrict__ W, int64_t ld, int64_t rows, int p, int PP,
+                                     const float *__restrict__ tcs, __half *__restrict__ Wb) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * PP) return;
+    const int j = (int)(e / rows);
+    const int64_t r = e % rows;
+    const float w = j < p ? W[r + (int64_t)j * ld] * tcs[0] : 0.0f;
+    const __half hi = __float2half_rn(w);
+    Wb[e] = hi;
+    Wb[(int64_t)PP * rows + e] = __float2half_rn(w - __half2float(hi));
+}
+
+// FP16 copy of a given FP32 Y: sy_c from the column maxima of Y (one CTA per column)
+__global__ void __launch_bounds__(256) y_scales_kernel(const float *__restrict__ Y, int64_t n, int PP, int p,
+                                                       float xscale, float *__restrict__ tcs) {
+    __shared__ float smax[256];
+    const int c = blockIdx.x;
+    float mx = 0.0f;
+    if (c < p)
+        for (int64_t i = threadIdx.x; i < n; i += 256) mx = fmaxf(mx, fabsf(Y[i * PP + c]));
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float sy = pow2_below(16384.0f, smax[0]);
+        tcs[2 + c] = sy;
+        tcs[2 + PP + c] = 1.0f / (xscale * sy);
+    }
+}
+
+__global__ void y_hilo_f16_kernel(const float *__restrict__ Y, int64_t n, int PP, const float *__restrict__ tcs,
+                                  __half *__restrict__ Yb, int64_t ldy) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * PP) return;
+    const int j = (int)(e / n);
+    const int64_t i = e % n;
+    const float y = Y[i * PP + j] * tcs[2 + j];
+    const __half hi = __float2half_rn(y);
+    Yb[(int64_t)j * ldy + i] = hi;
+    Yb[(int64_t)(PP + j) * ldy + i] = __float2half_rn(y - __half2float(hi));
+}
+
 __global__ void y_hilo_kernel(const float *__restrict__ Y, int64_t n, int PP, __nv_bfloat16 *__restrict__ Yb,
                               int64_t ldy) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -582,13 +701,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D BF16 tensor: dim0 (contiguous) = e0 elements, dim1 = e1, row pitch ld0
 // elements; box = b0 x b1; 128-byte swizzle; out-of-range reads return 0.
-CUtensorMap make_map(const void *base, uint64_t e0, uint64_t e1, uint64_t ld0, uint32_t b0, uint32_t b1) {
+CUtensorMap make_map(const void *base, uint64_t e0, uint64_t e1, uint64_t ld0, uint32_t b0, uint32_t b1,
+                     bool f16 = false) {
     CUtensorMap m;
     const cuuint64_t dims[2] = {e0, e1};
     const cuuint64_t strides[1] = {ld0 * 2};
     const cuuint32_t box[2] = {b0, b1};
     const cuuint32_t es[2] = {1, 1};
-    const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+    const CUresult r = encode_fn()(&m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                   const_cast<void *>(base), dims, strides,
                                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -636,6 +757,22 @@ void y_hilo(cudaStream_t s, const float *Y, int64_t n, int PP, __nv_bfloat16 *Yb
     LRA_LAUNCHED();
 }
 
+void pack_hilo_f16(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, float xscale,
+                   double xmaxnorm, float *tcs, __half *Wb) {
+    tc_scales_kernel<<<1, 256, 0, s>>>(W, ld, rows, p, PP, xscale, (float)xmaxnorm, tcs);
+    LRA_LAUNCHED();
+    pack_hilo_f16_kernel<<<(unsigned)ceil_div(rows * PP, 256), 256, 0, s>>>(W, ld, rows, p, PP, tcs, Wb);
+    LRA_LAUNCHED();
+}
+
+void y_hilo_f16(cudaStream_t s, const float *Y, int64_t n, int PP, int p, float xscale, float *tcs, __half *Yb,
+                int64_t ldy) {
+    y_scales_kernel<<<(unsigned)PP, 256, 0, s>>>(Y, n, PP, p, xscale, tcs);
+    LRA_LAUNCHED();
+    y_hilo_f16_kernel<<<(unsigned)ceil_div(n * PP, 256), 256, 0, s>>>(Y, n, PP, tcs, Yb, ldy);
+    LRA_LAUNCHED();
+}
+
 void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl) {
     const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 64);
     split_hilo_kernel<<<blocks, 256, 0, s>>>(X, count, Xh, Xl);
@@ -644,39 +781,41 @@ void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh
 
 int tc_rows_per_cta(int PP, bool pair) { return (!pair && PP >= 64) ? 2 * kBM : kBM; }
 
-void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err,
-            long long wait_cycles) {
+void xtw_tc(cudaStream_t s, const void *X, const void *Xl, int64_t dpad, int64_t n, const void *Wb, int PP,
+            float *Y32, void *Yb, int64_t ldy, int *err, long long wait_cycles, bool f16, const float *tcs) {
     const long long lim = wait_cycles > 0 ? wait_cycles : kWaitCycles;
-    const CUtensorMap mx = make_map(X, dpad, n, dpad, kBK, kBM);
-    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, kBK, kBM);
-    const CUtensorMap mw = make_map(Wb, dpad, 2 * PP, dpad, kBK, PP);
+    const CUtensorMap mx = make_map(X, dpad, n, dpad, kBK, kBM, f16);
+    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, kBK, kBM, f16);
+    const CUtensorMap mw = make_map(Wb, dpad, 2 * PP, dpad, kBK, PP, f16);
     const int nkb = (int)(dpad / kBK);
     const int rows = tc_rows_per_cta(PP, Xl != nullptr);
+    uint16_t *yb = static_cast<uint16_t *>(Yb);
     dispatch_tc_pp(PP, [&](auto ppc) {
         constexpr int P = decltype(ppc)::value;
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, rows), sm_count());
         auto launch = [&](auto kern, int smem) {
             ensure_smem(kern, (int)smem);
-            kern<<<grid, kThreads, smem, s>>>(mx, mxl, mw, nkb, n, Y32, Yb, ldy, err, lim);
+            kern<<<grid, kThreads, smem, s>>>(mx, mxl, mw, nkb, n, Y32, yb, ldy, err, lim, tcs);
             LRA_LAUNCHED();
         };
         if (Xl)
-            launch(xtw_tc_kernel<P, 2, 1>, Tile<P, 2, 1>::kSmem);
+            launch(xtw_tc_kernel<P, 2, 1, 1>, Tile<P, 2, 1>::kSmem);
+        else if (f16)
+            rows == kBM ? launch(xtw_tc_kernel<P, 1, 1, 0>, Tile<P, 1, 1>::kSmem)
+                        : launch(xtw_tc_kernel<P, 1, 2, 0>, Tile<P, 1, 2>::kSmem);
         else if (rows == kBM)
-            launch(xtw_tc_kernel<P, 1, 1>, Tile<P, 1, 1>::kSmem);
+            launch(xtw_tc_kernel<P, 1, 1, 1>, Tile<P, 1, 1>::kSmem);
         else
-            launch(xtw_tc_kernel<P, 1, 2>, Tile<P, 1, 2>::kSmem);
+            launch(xtw_tc_kernel<P, 1, 2, 1>, Tile<P, 1, 2>::kSmem);
     });
 }
 
-void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err,
-           long long wait_cycles) {
+void xy_tc(cudaStream_t s, const void *X, const void *Xl, int64_t dpad, int64_t n, const void *Yb, int64_t ldy,
+           int PP, float *Gp, int nchunks, int *err, long long wait_cycles, bool f16) {
     const long long lim = wait_cycles > 0 ? wait_cycles : kWaitCycles;
-    const CUtensorMap mx = make_map(X, dpad, n, dpad, 64, kBK);
-    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, 64, kBK);
-    const CUtensorMap my = make_map(Yb, n, 2 * PP, ldy, kBK, PP);
+    const CUtensorMap mx = make_map(X, dpad, n, dpad, 64, kBK, f16);
+    const CUtensorMap mxl = make_map(Xl ? Xl : X, dpad, n, dpad, 64, kBK, f16);
+    const CUtensorMap my = make_map(Yb, n, 2 * PP, ldy, kBK, PP, f16);
     const int64_t cpc = round_up(ceil_div(n, nchunks), kBK);
     const int rows = tc_rows_per_cta(PP, Xl != nullptr);
     dispatch_tc_pp(PP, [&](auto ppc) {
@@ -688,11 +827,14 @@ void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int6
             LRA_LAUNCHED();
         };
         if (Xl)
-            launch(xy_tc_kernel<P, 2, 1>, Tile<P, 2, 1>::kSmem);
+            launch(xy_tc_kernel<P, 2, 1, 1>, Tile<P, 2, 1>::kSmem);
+        else if (f16)
+            rows == kBM ? launch(xy_tc_kernel<P, 1, 1, 0>, Tile<P, 1, 1>::kSmem)
+                        : launch(xy_tc_kernel<P, 1, 2, 0>, Tile<P, 1, 2>::kSmem);
         else if (rows == kBM)
-            launch(xy_tc_kernel<P, 1, 1>, Tile<P, 1, 1>::kSmem);
+            launch(xy_tc_kernel<P, 1, 1, 1>, Tile<P, 1, 1>::kSmem);
         else
-            launch(xy_tc_kernel<P, 1, 2>, Tile<P, 1, 2>::kSmem);
+            launch(xy_tc_kernel<P, 1, 2, 1>, Tile<P, 1, 2>::kSmem);
     });
 }
 

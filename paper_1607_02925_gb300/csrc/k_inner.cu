@@ -47,7 +47,8 @@ template <typename TX, int S, int PC>
 __global__ void __launch_bounds__(32) svrg_inner_pair_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, float eta, float lam,
+    float etac) {
     constexpr int R = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TX *ring = reinterpret_cast<TX *>(smem_raw);  // [R][dpad]
@@ -90,15 +91,7 @@ __global__ void __launch_bounds__(32) svrg_inner_pair_kernel(
         for (int s = 0; s < S; ++s) {
             const int64_t r = 4 * ((int64_t)lane + 32 * s);
             if (t < m && r < dpad) {
-                if constexpr (sizeof(TX) == 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
-                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
-                } else {
-                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
-                }
+                load4_f32(slot + r, x[s]);
             } else {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
@@ -158,8 +151,8 @@ __global__ void __launch_bounds__(32) svrg_inner_pair_kernel(
         cp_async_wait<R - 2>();
         load(t + 1, x1);
         load(t + 2, x2);
-        const float c0 = eta * cval[t];
-        const float c1v = (t + 1 < m) ? eta * cval[t + 1] : 0.0f;
+        const float c0 = etac * cval[t];
+        const float c1v = (t + 1 < m) ? etac * cval[t + 1] : 0.0f;
         float ct[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
@@ -218,7 +211,8 @@ template <typename TX, int S, int PC>
 __global__ void __launch_bounds__(512) svrg_inner1_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, float eta, float lam,
+    float etac) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TX *ring = reinterpret_cast<TX *>(smem_raw);  // [kRing][dpad]
     __shared__ float red[2][16][PC];
@@ -274,15 +268,7 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
         for (int s = 0; s < S; ++s) {
             const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
             if (r < dpad) {
-                if constexpr (sizeof(TX) == 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
-                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
-                } else {
-                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
-                }
+                load4_f32(slot + r, x[s]);
             } else {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
@@ -303,7 +289,7 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
         if (nwarps == 1) {
             // one warp: every lane already holds the full sum (no barrier)
 #pragma unroll
-            for (int j = 0; j < PC; ++j) coef[j] = eta * ci * part[j];
+            for (int j = 0; j < PC; ++j) coef[j] = etac * ci * part[j];
         } else {
             const int buf = (int)(t & 1);
             if (lane == 0) {
@@ -315,7 +301,7 @@ __global__ void __launch_bounds__(512) svrg_inner1_kernel(
             for (int j = 0; j < PC; ++j) {
                 float rj = 0.0f;
                 for (int w = 0; w < nwarps; ++w) rj += red[buf][w][j];
-                coef[j] = eta * ci * rj;
+                coef[j] = etac * ci * rj;
             }
         }
 #pragma unroll
@@ -433,7 +419,8 @@ template <typename TX, int S, int PC, int NW, int R = la_ring<TX, S>()>
 __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, float eta, float lam,
+    float etac) {
     constexpr int NV = 4 * PC + 2;  // uA, wA, uB, wB per column, then vA, vB
     constexpr int NP = pow2_at_least<NV>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -485,16 +472,10 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
         for (int s = 0; s < S; ++s) {
             const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
             if (t < m && r < dpad) {
-                if constexpr (sizeof(TX) == 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
-                    x[s][0] = make_float2(q.x, q.y);
-                    x[s][1] = make_float2(q.z, q.w);
-                } else {
-                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
-                    const __nv_bfloat162 *e = reinterpret_cast<const __nv_bfloat162 *>(&q);
-                    x[s][0] = __bfloat1622float2(e[0]);
-                    x[s][1] = __bfloat1622float2(e[1]);
-                }
+                float q[4];
+                load4_f32(slot + r, q);
+                x[s][0] = make_float2(q[0], q[1]);
+                x[s][1] = make_float2(q[2], q[3]);
             } else {
                 x[s][0] = make_float2(0.0f, 0.0f);
                 x[s][1] = make_float2(0.0f, 0.0f);
@@ -568,8 +549,8 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
         cp_async_wait<R - 2>();
         load(t + 1, x1);
         load(t + 2, x2);
-        const float c0 = eta * cval[t];
-        const float c1v = (t + 1 < m) ? eta * cval[t + 1] : 0.0f;
+        const float c0 = etac * cval[t];
+        const float c1v = (t + 1 < m) ? etac * cval[t + 1] : 0.0f;
         float ct[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
@@ -625,7 +606,8 @@ template <typename TX, int S, int NB, int D>
 __global__ void __launch_bounds__(512) svrg_inner_batch_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
-    const float *__restrict__ cval, int64_t m, float eta, float lam) {
+    const float *__restrict__ cval, int64_t m, float eta, float lam,
+    float etac) {
     constexpr int PC = 1, MB = NB, nb = NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TX *ring = reinterpret_cast<TX *>(smem_raw);  // [D * NB][dpad]
@@ -677,15 +659,7 @@ __global__ void __launch_bounds__(512) svrg_inner_batch_kernel(
         for (int s = 0; s < S; ++s) {
             const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
             if (r < dpad) {
-                if constexpr (sizeof(TX) == 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(slot + r);
-                    x[s][0] = q.x; x[s][1] = q.y; x[s][2] = q.z; x[s][3] = q.w;
-                } else {
-                    const uint2 q = *reinterpret_cast<const uint2 *>(slot + r);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) x[s][v] = __bfloat162float(e[v]);
-                }
+                load4_f32(slot + r, x[s]);
             } else {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) x[s][v] = 0.0f;
@@ -738,7 +712,7 @@ __global__ void __launch_bounds__(512) svrg_inner_batch_kernel(
                 for (int j = 0; j < PC; ++j) {
                     float rj = 0.0f;
                     for (int w = 0; w < nwarps; ++w) rj += red[buf][w][u * PC + j];
-                    coef[u][j] = eta * cu * rj * invb;
+                    coef[u][j] = etac * cu * rj * invb;
                 }
             }
         }
@@ -790,23 +764,23 @@ __global__ void __launch_bounds__(512) svrg_inner_batch_kernel(
 template <typename TX, int S, int PC>
 void launch_inner1(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                    const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                   float eta, float lam, int nt) {
+                   float eta, float lam, float etac, int nt) {
     auto k = svrg_inner1_kernel<TX, S, PC>;
     const size_t smem = (size_t)kRing * dpad * sizeof(TX);
     ensure_smem(k, (int)smem);
     const unsigned grid = (unsigned)ceil_div(p, PC);
-    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    k<<<grid, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac);
     LRA_LAUNCHED();
 }
 
 template <typename TX, int S, int PC>
 void launch_la(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W, const float *Wt,
-               const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam, int nt) {
+               const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam, float etac, int nt) {
     constexpr int R = la_ring<TX, S>();
     const size_t smem = (size_t)R * dpad * sizeof(TX);
     auto go = [&](auto k) {
         ensure_smem(k, (int)smem);
-        k<<<(unsigned)ceil_div(p, PC), nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+        k<<<(unsigned)ceil_div(p, PC), nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac);
         LRA_LAUNCHED();
     };
     if (nt <= 256)
@@ -818,11 +792,11 @@ void launch_la(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p,
 template <typename TX, int S, int NB, int D>
 void launch_batch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                   const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                  float eta, float lam, int nt) {
+                  float eta, float lam, float etac, int nt) {
     auto k = svrg_inner_batch_kernel<TX, S, NB, D>;
     const size_t smem = (size_t)D * NB * dpad * sizeof(TX);
     ensure_smem(k, (int)smem);
-    k<<<(unsigned)p, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    k<<<(unsigned)p, nt, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac);
     LRA_LAUNCHED();
 }
 
@@ -833,18 +807,19 @@ constexpr size_t kRingBytes = 220 * 1024;
 
 template <typename TX, int S, int PC>
 void launch_pair(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W, const float *Wt,
-                 const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam) {
+                 const float *M, const int32_t *idx, const float *cval, int64_t m, float eta, float lam,
+                 float etac) {
     auto k = svrg_inner_pair_kernel<TX, S, PC>;
     const size_t smem = (size_t)8 * dpad * sizeof(TX);
     ensure_smem(k, (int)smem);
-    k<<<(unsigned)ceil_div(p, PC), 32, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);
+    k<<<(unsigned)ceil_div(p, PC), 32, smem, st>>>((const TX *)X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac);
     LRA_LAUNCHED();
 }
 
 template <typename TX>
 void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, int p, float *W,
                     const float *Wt, const float *M, const int32_t *idx, const float *cval, int64_t m,
-                    int nb, float eta, float lam) {
+                    int nb, float eta, float lam, float etac) {
     // threads: 4 rows each, at most 512; S = row groups per thread.  Up to
     // d = 512 the one-sample step runs on a single warp (S <= 4): its x_i^T Delta
     // is then reduced by shuffles alone, without a block barrier per step
@@ -871,7 +846,7 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
             // a single warp: two steps per iteration with the look-ahead identity
 #define LRA_PAIR_CASE(SS, PCC)                                                                          \
     if (S == SS && pc == PCC) {                                                                         \
-        launch_pair<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam);               \
+        launch_pair<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac);               \
         return;                                                                                         \
     }
             LRA_PAIR_CASE(1, 1)
@@ -898,7 +873,7 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
         const int pcl = (p <= 64 || S > 2) ? 1 : 2;
 #define LRA_LA_CASE(SS, PCC)                                                                    \
     if (S == SS && pcl == PCC) {                                                                \
-        launch_la<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);     \
+        launch_la<TX, SS, PCC>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac, nt);     \
         return;                                                                                 \
     }
         LRA_LA_CASE(1, 1)
@@ -911,9 +886,9 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
         // d > 8192: the look-ahead kernel's three column buffers would spill;
         // one barrier per step
         if (S <= 6) {
-            launch_inner1<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+            launch_inner1<TX, 6, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac, nt);
         } else {
-            launch_inner1<TX, 8, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+            launch_inner1<TX, 8, 1>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac, nt);
         }
         return;
     }
@@ -938,9 +913,9 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
     auto go = [&](auto sc, auto nbc) {
         constexpr int SS = decltype(sc)::value, NBB = decltype(nbc)::value;
         if (depth == 4)
-            launch_batch<TX, SS, NBB, 4>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+            launch_batch<TX, SS, NBB, 4>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac, nt);
         else
-            launch_batch<TX, SS, NBB, 2>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, nt);
+            launch_batch<TX, SS, NBB, 2>(st, X, ldx, dpad, p, W, Wt, M, idx, cval, m, eta, lam, etac, nt);
     };
     using std::integral_constant;
     auto by_nb = [&](auto sc) {
@@ -969,16 +944,21 @@ void inner_dispatch(cudaStream_t st, const void *X, int64_t ldx, int64_t dpad, i
 
 void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
                 float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
-                int64_t m, float eta, float lam, int batch) {
+                int64_t m, float eta, float lam, int batch, float cscale) {
     if (m <= 0) return;  // an empty step sequence leaves W unchanged
     if (batch < 1 || batch > 16 || (batch & (batch - 1)) != 0) {
         set_error("batch must be a power of two in [1, 16]");
         throw Error{LRA_EINVAL};
     }
+    // a stored X scaled by sigma (FP16 storage) gives r sigma times the true r;
+    // c_i / sigma^2 in the stochastic term keeps every step the true one
+    const float etac = eta * cscale;
     if (dt == LRA_BF16)
-        inner_dispatch<__nv_bfloat16>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam);
+        inner_dispatch<__nv_bfloat16>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam, etac);
+    else if (dt == LRA_F16)
+        inner_dispatch<__half>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam, etac);
     else
-        inner_dispatch<float>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam);
+        inner_dispatch<float>(s, X, ldx, dpad, p, W, Wt, M, idx, cval, m, batch, eta, lam, etac);
 }
 
 }  // namespace lra

@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 #include "kernels.cuh"
 
@@ -15,7 +17,7 @@ namespace lra {
 // ---------------------------------------------------------------------------
 template <typename TX>
 __global__ void __launch_bounds__(256) colnorms_kernel(const TX *__restrict__ X, int64_t ldx,
-                                                       int64_t rows, int64_t n,
+                                                       int64_t rows, int64_t n, double inv2,
                                                        double *__restrict__ norm2) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -33,18 +35,62 @@ __global__ void __launch_bounds__(256) colnorms_kernel(const TX *__restrict__ X,
         }
     }
     acc = warp_sum(acc);
-    if (lane == 0) norm2[i] = acc;
+    if (lane == 0) norm2[i] = acc * inv2;
 }
 
 void colnorms(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t d, int64_t n,
-              double *norm2) {
+              double *norm2, double xscale) {
     (void)d;
     const int64_t rows = ldx;  // padding rows are zero
     dim3 grid((unsigned)ceil_div(n, 8));
+    const double inv2 = 1.0 / (xscale * xscale);  // a power of two: exact
     if (dt == LRA_BF16)
-        colnorms_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)X, ldx, rows, n, norm2);
+        colnorms_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)X, ldx, rows, n, inv2, norm2);
+    else if (dt == LRA_F16)
+        colnorms_kernel<__half><<<grid, 256, 0, s>>>((const __half *)X, ldx, rows, n, inv2, norm2);
     else
-        colnorms_kernel<float><<<grid, 256, 0, s>>>((const float *)X, ldx, rows, n, norm2);
+        colnorms_kernel<float><<<grid, 256, 0, s>>>((const float *)X, ldx, rows, n, inv2, norm2);
+    LRA_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------
+// FP16 storage: max |x| over the FP32 copy (non-negative floats compare as
+// their bit patterns, so an atomicMax on the bits is exact and order-free),
+// then fp16(xscale x) with xscale = 2^(14 - floor(log2 max)).
+// ---------------------------------------------------------------------------
+__global__ void maxabs_kernel(const float *__restrict__ X, int64_t count, unsigned *__restrict__ out) {
+    float mx = 0.0f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(X[e]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+__global__ void to_f16_kernel(const float *__restrict__ X, int64_t count, float xscale, __half *__restrict__ Xs) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        Xs[e] = __float2half_rn(X[e] * xscale);
+}
+
+float f16_storage_scale(cudaStream_t s, const float *X32, int64_t count, unsigned *scratch) {
+    LRA_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned), s));
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16);
+    maxabs_kernel<<<blocks, 256, 0, s>>>(X32, count, scratch);
+    LRA_LAUNCHED();
+    unsigned bits = 0;
+    LRA_CUDA(cudaMemcpyAsync(&bits, scratch, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    LRA_CUDA(cudaStreamSynchronize(s));
+    float mx;
+    std::memcpy(&mx, &bits, sizeof(mx));
+    if (!(mx > 0.0f) || !std::isfinite(mx)) return 1.0f;
+    int e = 0;
+    std::frexp(mx, &e);  // mx in [2^(e-1), 2^e)
+    return std::ldexp(1.0f, 15 - e);
+}
+
+void to_f16(cudaStream_t s, const float *X32, int64_t count, float xscale, __half *Xs) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 64);
+    to_f16_kernel<<<blocks, 256, 0, s>>>(X32, count, xscale, Xs);
     LRA_LAUNCHED();
 }
 

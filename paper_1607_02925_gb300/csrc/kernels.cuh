@@ -12,7 +12,11 @@ namespace lra {
 
 // ---- setup (k_setup.cu) ---------------------------------------------------
 void colnorms(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t d, int64_t n,
-              double *norm2);
+              double *norm2, double xscale = 1.0);
+// FP16 storage: the power of two that puts max |x| of X32 (count entries) in
+// [2^14, 2^15) (scratch: one device word; synchronises s), and X16 = fp16(xscale X32)
+float f16_storage_scale(cudaStream_t s, const float *X32, int64_t count, unsigned *scratch);
+void to_f16(cudaStream_t s, const float *X32, int64_t count, float xscale, __half *Xs);
 // out[0] = sum_i v_i (fixed-order), out[1] = max_i v_i; scratch >= 2 * 1024 doubles
 void sum_max(cudaStream_t s, const double *v, int64_t n, double *out, double *scratch);
 // Integer weights, their inclusive prefix sums (cum), c_i = total / w_i and
@@ -50,7 +54,8 @@ void xy(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, 
 // scratch then holds 3 doubles per 16 rows)
 void anchor_epilogue(cudaStream_t s, const float *Gp, int nchunks, int64_t dpad, int PP, int p,
                      double lam, const float *Wt, const float *B, float *M, double *norms,
-                     double *scratch, const float *Z = nullptr, double gamma = 0.0);
+                     double *scratch, const float *Z = nullptr, double gamma = 0.0,
+                     const float *colscale = nullptr);
 
 // ---- anchor pass on tensor cores, BF16 X (k_anchor_tc.cu) ---------------
 // leading dimension of the hi/lo BF16 copy of Y (n rounded up to 64)
@@ -67,19 +72,25 @@ void y_hilo(cudaStream_t s, const float *Y, int64_t n, int PP, __nv_bfloat16 *Yb
 void split_hilo(cudaStream_t s, const float *X, int64_t count, __nv_bfloat16 *Xh, __nv_bfloat16 *Xl);
 // Y = X^T W on tcgen05: writes Y32 (n x PP row-major) and/or Yb (hi/lo) when
 // non-null.  X is BF16 (Xl == nullptr) or the BF16 pair (X, Xl) of an FP32 X.
-void xtw_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-            const __nv_bfloat16 *Wb, int PP, float *Y32, __nv_bfloat16 *Yb, int64_t ldy, int *err,
-            long long wait_cycles = 0);
-// partial G = X Y per column chunk on tcgen05 (same Gp layout as xy)
-void xy_tc(cudaStream_t s, const __nv_bfloat16 *X, const __nv_bfloat16 *Xl, int64_t dpad, int64_t n,
-           const __nv_bfloat16 *Yb, int64_t ldy, int PP, float *Gp, int nchunks, int *err,
-           long long wait_cycles = 0);
+void xtw_tc(cudaStream_t s, const void *X, const void *Xl, int64_t dpad, int64_t n, const void *Wb, int PP,
+            float *Y32, void *Yb, int64_t ldy, int *err, long long wait_cycles = 0, bool f16 = false,
+            const float *tcs = nullptr);
+// partial G = X Y per column chunk on tcgen05 (same Gp layout as xy); with
+// FP16 operands column c of each partial carries the factor xscale sy_c
+void xy_tc(cudaStream_t s, const void *X, const void *Xl, int64_t dpad, int64_t n, const void *Yb, int64_t ldy,
+           int PP, float *Gp, int nchunks, int *err, long long wait_cycles = 0, bool f16 = false);
+// FP16 operands (FP16 storage): scales into tcs (2 + 2 PP floats: see the
+// tensor-core kernels) and the FP16 hi / lo small operand
+void pack_hilo_f16(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, float xscale,
+                   double xmaxnorm, float *tcs, __half *Wb);
+void y_hilo_f16(cudaStream_t s, const float *Y, int64_t n, int PP, int p, float xscale, float *tcs, __half *Yb,
+                int64_t ldy);
 
 // ---- SVRG inner loop (k_inner.cu) -----------------------------------------
 // m steps of `batch` samples each (idx, cval: m * batch entries); batch a power of two <= 16
 void svrg_inner(cudaStream_t s, const void *X, lra_dtype dt, int64_t ldx, int64_t dpad, int p,
                 float *W, const float *Wt, const float *M, const int32_t *idx, const float *cval,
-                int64_t m, float eta, float lam, int batch = 1);
+                int64_t m, float eta, float lam, int batch = 1, float cscale = 1.0f);
 
 // ---- p x p and d x p helpers (k_small.cu) -------------------------------
 // G (p x p FP64, column-major) = A^T A, A rows x p with strides (rs, cs).

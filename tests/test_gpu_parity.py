@@ -75,6 +75,24 @@ def bf16_values(x32):
     return r.astype(np.uint32).view(np.float32)
 
 
+def f16_values(x32):
+    """The values an FP16-stored matrix holds: fp16(s x) / s with s the power of
+    two that puts max |x| in [2^14, 2^15), rounded to nearest even."""
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    mx = float(np.max(np.abs(x32)))
+    e = math.frexp(mx)[1]
+    sc = math.ldexp(1.0, 15 - e)
+    return ((x32.astype(np.float64) * sc).astype(np.float16).astype(np.float64) / sc)
+
+
+def stored_values(Xt, storage):
+    if storage == lra.LRA_BF16:
+        return bf16_values(Xt)
+    if storage == lra.LRA_F16:
+        return f16_values(Xt)
+    return Xt
+
+
 # ragged d, n, p; p = 100 and 64 take the two-M-tile tensor-core kernels for BF16
 # X (d = 520 -> 5 row tiles of 128: the last CTA's second tile lies past dpad)
 SHAPES = [(300, 3000, 13), (256, 2048, 10), (128, 777, 40), (520, 1500, 48), (520, 1500, 100),
@@ -85,12 +103,14 @@ SHAPES = [(300, 3000, 13), (256, 2048, 10), (128, 777, 40), (520, 1500, 48), (52
 # a0: column norms, sampling table, sampler
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16])
+@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16, lra.LRA_F16])
 def test_colnorms(ctx, storage):
     Xt, _, _ = planted(300, 3001, 5, 1)
     if storage == lra.LRA_BF16:
         Xt = bf16_values(Xt)
     m = Mat(ctx, Xt, storage)
+    if storage == lra.LRA_F16:
+        Xt = f16_values(Xt)
     try:
         n2 = torch.zeros(m.n, dtype=torch.float64, device=DEV)
         fro2 = lra.lra_colnorms(m.h, n2)
@@ -141,7 +161,7 @@ def test_gaussian_block(ctx):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("d,n,p", SHAPES)
-@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16])
+@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16, lra.LRA_F16])
 def test_anchor_matches_oracle(ctx, d, n, p, storage):
     Xt, _, _ = planted(d, n, 5, d + n)
     if storage == lra.LRA_BF16:
@@ -151,6 +171,8 @@ def test_anchor_matches_oracle(ctx, d, n, p, storage):
     B = rng.standard_normal((d, p)).astype(np.float32)
     lam = 1.7
     m = Mat(ctx, Xt, storage)
+    if storage == lra.LRA_F16:
+        Xt = f16_values(Xt)
     try:
         M = torch.zeros(p, d, dtype=torch.float32, device=DEV)
         nM2, nB2 = lra.lra_anchor(m.h, p, dev_block(Wt), dev_block(B), lam, M)
@@ -294,11 +316,11 @@ def test_sym_eig(ctx, p):
     assert np.max(np.abs(Vg.T @ Vg - np.eye(p))) < 1e-12
 
 
-@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16])
+@pytest.mark.parametrize("storage", [lra.LRA_F32, lra.LRA_BF16, lra.LRA_F16])
 def test_rayleigh_ritz(ctx, storage):
     d, n, p = 300, 3000, 13
     Xt, U, s = planted(d, n, 5, 19)
-    X_st = bf16_values(Xt) if storage == lra.LRA_BF16 else Xt
+    X_st = stored_values(Xt, storage)
     S = O.orth(np.random.default_rng(1).standard_normal((d, p)))
     m = Mat(ctx, Xt, storage)
     try:
@@ -453,6 +475,55 @@ def test_solve_bf16_storage_matches_oracle(ctx):
     ref = O.solve(Xb, 5, 10, 1e-3, 3, O.Options(shift_policy=O.SHIFT_FAR, **sched), Xt_final=Xt)
     assert O.sin_angle(ref.U, Ug) < 1e-3
     assert np.max(np.abs(rg - ref.ritz) / ref.ritz) < 1e-4
+
+
+def test_solve_f16_storage_matches_oracle(ctx):
+    """FP16 storage (fp16(s x), s a power of two) on a fixed schedule against the
+    oracle run on the FP16-representable values, the final Rayleigh-Ritz step on
+    the FP32 values; and the default stop rule meets the ratio."""
+    Xt, U, s = planted(256, 2048, 5, 9)
+    Xh = f16_values(Xt)
+    sched = dict(min_outer=10, max_outer=10, fixed_epochs=5)
+    st, Ug, rg, rep = run_solve(ctx, Xt, 5, 10, 3, storage=lra.LRA_F16, shift_policy=lra.LRA_SHIFT_FAR, **sched)
+    ref = O.solve(Xh, 5, 10, 1e-3, 3, O.Options(shift_policy=O.SHIFT_FAR, **sched), Xt_final=Xt)
+    assert O.sin_angle(ref.U, Ug) < 1e-4
+    assert np.max(np.abs(rg - ref.ritz) / ref.ritz) < 1e-5
+    st, Ug, rg, rep = run_solve(ctx, Xt, 5, 10, 3, storage=lra.LRA_F16, shift_policy=lra.LRA_SHIFT_FAR)
+    assert st == 0
+    ratio = O.frobenius_error(Xt, Ug) / L.closed_form_opt(s, 5)
+    assert ratio <= 1.0 + 1e-3
+
+
+def test_f16_storage_inner_loop_and_scale(ctx):
+    """The inner loop on an FP16-stored X (stored as fp16(s x)) equals the
+    oracle's epoch on the FP16-representable values, for a matrix whose entries
+    lie far below FP16's normal range before the scale s."""
+    d, n, p = 700, 2000, 6
+    Xt, _, _ = planted(d, n, 5, 31)
+    Xt = np.ascontiguousarray((Xt * 1e-4).astype(np.float32))   # entries ~1e-7: FP16 subnormal unscaled
+    Xh = f16_values(Xt)
+    rng = np.random.default_rng(3)
+    Wt = rng.standard_normal((d, p)).astype(np.float32)
+    M = (0.1 * rng.standard_normal((d, p))).astype(np.float32)
+    W0 = (Wt + 0.05 * rng.standard_normal((d, p))).astype(np.float32)
+    steps = 500
+    idx = rng.integers(0, n, size=steps).astype(np.int32)
+    c = (rng.uniform(0.5, 2.0, size=n) * n * 2e7).astype(np.float32)
+    eta, lam = 0.02, 1.3
+    m = Mat(ctx, Xt, lra.LRA_F16)
+    try:
+        W = dev_block(W0)
+        lra.lra_svrg_inner(m.h, p, W, dev_block(Wt), dev_block(M), torch.from_numpy(idx).to(DEV),
+                           steps, torch.from_numpy(c).to(DEV), eta, lam)
+        ref = O.svrg_epoch(Xh, W0.astype(np.float64), Wt.astype(np.float64), M.astype(np.float64),
+                           idx.astype(np.int64), c.astype(np.float64), eta, lam)
+        assert rel(cm(W) - Wt, ref - Wt) < 1e-5
+        assert elem_rms(cm(W) - Wt, ref - Wt) < 1e-5
+        n2 = torch.zeros(n, dtype=torch.float64, device=DEV)
+        lra.lra_colnorms(m.h, n2)
+        assert rel(n2.cpu().numpy(), np.sum(Xh * Xh, axis=1)) < 1e-13
+    finally:
+        m.close()
 
 
 def test_edge_cases_and_errors(ctx):
