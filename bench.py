@@ -74,6 +74,10 @@ def parse_args():
     ap.add_argument("--serve", action="store_true", help="request-loop benchmark instead")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-mean-ms", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=0,
+                    help="worker streams of the request loop (0: the library's default, LRA_SERVE_SLOTS or 8)")
+    ap.add_argument("--serve-no-baseline", action="store_true",
+                    help="leave out the one-job-at-a-time baseline of the request-loop benchmark")
     return ap.parse_args()
 
 
@@ -736,6 +740,8 @@ def serve_benchmark(args, local):
 
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
+    if args.serve_slots > 0:
+        os.environ["LRA_SERVE_SLOTS"] = str(args.serve_slots)
     rng = np.random.default_rng(5)
     nreq = args.serve_requests
     arrivals = np.cumsum(rng.exponential(args.serve_mean_ms / 1e3, size=nreq))
@@ -864,7 +870,7 @@ def serve_benchmark(args, local):
     ctx = lra.lra_init(local)
     tb = 0.0
     blat = []
-    for j, q in enumerate(reqs):
+    for j, q in enumerate([] if args.serve_no_baseline else reqs):
         start = max(tb, arrivals[j])
         ts = time.perf_counter()
         m = make(ctx, q, lra.LRA_F32)
@@ -875,7 +881,7 @@ def serve_benchmark(args, local):
         tb = start + (time.perf_counter() - ts)
         blat.append(tb - arrivals[j])
     lra.lra_finalize(ctx)
-    blat = np.array(blat)
+    blat = np.array(blat if blat else [float("nan")])
     del pool
     torch.cuda.empty_cache()
     return {
@@ -887,7 +893,7 @@ def serve_benchmark(args, local):
         "statuses": sorted({int(r[0]) for r in results}),
         "baseline_one_at_a_time_f32": {"p50": float(np.percentile(blat, 50)),
                                         "p99": float(np.percentile(blat, 99)),
-                                        "jobs_per_s": nreq / (tb - arrivals[0])},
+                                        "jobs_per_s": (nreq / (tb - arrivals[0])) if tb > 0 else None},
         "config": {"workload": "planted small-gap spectrum rescaled to k; d in {256,1024,4096}, "
                                "n in {8192,65536,262144}, k in {5,10,20,50}, p = 2k, FP32/BF16 1:1",
                    "shift": "far", "eps": args.eps, "slots": int(os.environ.get("LRA_SERVE_SLOTS", "8"))},
