@@ -492,7 +492,11 @@ void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
     // the X passes stream X through the tensor cores.
     LRA_CUDA(cudaEventRecord(ws_.ev_fork, s_));
     LRA_CUDA(cudaStreamWaitEvent(ws_.side, ws_.ev_fork, 0));
-    gram64(ws_.side, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr2, tc(use32));
+    // the basis as the tensor-core pass used it: its BF16 pair for FP32 and BF16
+    // storage; FP16 storage splits it into FP16 hi/lo of a power-of-two multiple,
+    // whose sum is S to about 2^-22, so S itself is used there
+    const bool bf16_pair = tc(use32) && mat_->storage != LRA_F16;
+    gram64(ws_.side, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr2, bf16_pair);
     LRA_CUDA(cudaEventRecord(ws_.ev_join, ws_.side));
     xt_mul(S, p, ws_.Q, use32, with_xq);
     if (with_xq) {
@@ -500,7 +504,7 @@ void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
         // matrix from a d-long contraction instead of the n-long Q^T Q
         x_mul(tc(use32) ? nullptr : ws_.Q, p, ws_.T1, use32);
         if (timer) timer->begin(KernelTimer::RITZ, p);
-        if (tc(use32))
+        if (bf16_pair)
             cross_gram(s_, nullptr, ws_.Wb, ws_.Wb + (size_t)PP * mat_->dpad, ws_.T1, mat_->dpad, mat_->dpad, p,
                        ws_.H, ws_.gscr);
         else
