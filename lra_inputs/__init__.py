@@ -146,6 +146,17 @@ def planted_numpy(d: int, n: int, sigma: np.ndarray, seed: int):
     return Xt, U, np.asarray(sigma, dtype=np.float64)
 
 
+def _qr(a):
+    """QR of a torch matrix on its device; on the host when the device's linear
+    algebra library cannot be loaded (as under a profiler), moved back after."""
+    import torch
+    try:
+        return torch.linalg.qr(a)
+    except RuntimeError:
+        q, r = torch.linalg.qr(a.cpu())
+        return q.to(a.device), r.to(a.device)
+
+
 def planted_torch(d: int, n: int, sigma: np.ndarray, seed: int, device="cpu",
                   dtype=None, chunk: int = 1 << 16):
     """X = U diag(sigma) V^T generated with torch (for sizes that need a GPU).
@@ -166,11 +177,11 @@ def planted_torch(d: int, n: int, sigma: np.ndarray, seed: int, device="cpu",
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
         gu = torch.randn(d, r, generator=gen, device=device, dtype=torch.float32)
-        qu, ru = torch.linalg.qr(gu)
+        qu, ru = _qr(gu)
         qu = qu * torch.sign(torch.diagonal(ru))[None, :]
         del gu, ru
         gv = torch.randn(n, r, generator=gen, device=device, dtype=torch.float32)
-        qv, rv = torch.linalg.qr(gv)
+        qv, rv = _qr(gv)
         qv = qv * torch.sign(torch.diagonal(rv))[None, :]
         del gv, rv
         sig = torch.as_tensor(np.asarray(sigma), device=device, dtype=torch.float32)

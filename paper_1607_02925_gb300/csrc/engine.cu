@@ -101,7 +101,7 @@ size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items) {
     b += 2 * sizeof(float) * n * PP;            // Q Y
     b += sizeof(float) * (size_t)nch * dpad * PP;  // Gp
     b += sizeof(double) * (9 * pmax * pmax + gram_scratch(pmax) + dpad);
-    b += sizeof(float) * (2 + 2 * (size_t)PP);  // scales of FP16 tensor-core operands
+    b += sizeof(float) * (2 + 3 * (size_t)PP);  // scales of FP16 tensor-core operands
     if (sp_items >= 0)
         b += sizeof(float) * (size_t)sp_items * PP;                 // partial
     else
@@ -156,7 +156,7 @@ Workspace::Workspace(lra_ctx *c, int64_t dpad_, int64_t n_, int pmax_, cudaStrea
         status = alloc<int>(4);
         tcerr = alloc<int>(4);
         zero(tcerr, sizeof(int) * 4);
-        tcs = alloc<float>(2 + 2 * (size_t)PPmax);
+        tcs = alloc<float>(2 + 3 * (size_t)PPmax);
         if (sp_items >= 0) {
             partial = alloc<float>((size_t)std::max<int64_t>(sp_items, 1) * PPmax);
         } else {

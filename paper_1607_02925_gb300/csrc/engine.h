@@ -164,7 +164,7 @@ struct Workspace {
     int64_t ldy = 0;
     int *status = nullptr;
     int *tcerr = nullptr;  // error word of the tensor-core kernels
-    float *tcs = nullptr;  // scales of the FP16 tensor-core operands (2 + 2 PPmax)
+    float *tcs = nullptr;  // scales of the FP16 tensor-core operands (2 + 3 PPmax)
     int32_t *idx = nullptr;
     float *cval = nullptr;
     int64_t idx_cap = 0;

@@ -568,7 +568,7 @@ __global__ void split_hilo_kernel(const float *__restrict__ X, int64_t count, __
 }
 
 // Yb (hi/lo, column-major, leading dim ldy) from Y (n x PP row-major FP32)
-// FP16 operands (FP16 storage): scales from the block W (one CTA).  sw puts
+// FP16 operands (FP16 storage): scales from the block W.  sw puts
 // max |w| in [2^13, 2^14); sy_c bounds column c of Y = X^T W through
 // |y_ic| <= ||x_i|| ||w_c|| <= sqrt(max_i ||x_i||^2) ||w_c|| and puts the bound
 // in [2^13, 2^14), so the FP16 hi / lo copy of Y never overflows and its
@@ -581,43 +581,50 @@ __device__ __forceinline__ float pow2_below(float target, float v) {
     return ldexpf(1.0f, e - 1);
 }
 
-__global__ void __launch_bounds__(256) tc_scales_kernel(const float *__restrict__ W, int64_t ld, int64_t rows, int p,
-                                                        int PP, float xscale, float xmaxnorm,
-                                                        float *__restrict__ tcs) {
+// Per column c (one CTA each): ||w_c|| gives sy_c; max |w_c| goes to
+// tcs[2 + 2 PP + c] for the block maximum taken by tc_sw_kernel.
+__global__ void __launch_bounds__(256) tc_colstats_kernel(const float *__restrict__ W, int64_t ld, int64_t rows,
+                                                          int p, int PP, float xscale, float xmaxnorm,
+                                                          float *__restrict__ tcs) {
     __shared__ float smax[256];
     __shared__ double snorm[256];
+    const int c = blockIdx.x;
     float mx = 0.0f;
-    for (int64_t e = threadIdx.x; e < rows * p; e += 256) mx = fmaxf(mx, fabsf(W[(e % rows) + (e / rows) * ld]));
+    double a = 0.0;
+    if (c < p)
+        for (int64_t r = threadIdx.x; r < rows; r += 256) {
+            const float w = W[r + (int64_t)c * ld];
+            mx = fmaxf(mx, fabsf(w));
+            a += (double)w * (double)w;
+        }
     smax[threadIdx.x] = mx;
+    snorm[threadIdx.x] = a;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+        if ((int)threadIdx.x < w) {
+            smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+            snorm[threadIdx.x] += snorm[threadIdx.x + w];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const float sw = pow2_below(16384.0f, smax[0]);
+        const float sy = pow2_below(16384.0f, xmaxnorm * (float)sqrt(snorm[0]));
+        tcs[2 + c] = sy;
+        tcs[2 + PP + c] = 1.0f / (xscale * sy);
+        tcs[2 + 2 * PP + c] = smax[0];
+    }
+}
+
+// sw from the column maxima (one warp, fixed order)
+__global__ void tc_sw_kernel(int PP, float xscale, float *__restrict__ tcs) {
+    float mx = 0.0f;
+    for (int c = threadIdx.x; c < PP; c += 32) mx = fmaxf(mx, tcs[2 + 2 * PP + c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) {
+        const float sw = pow2_below(16384.0f, mx);
         tcs[0] = sw;
         tcs[1] = 1.0f / (xscale * sw);
-    }
-    for (int c = 0; c < PP; ++c) {
-        double a = 0.0;
-        if (c < p)
-            for (int64_t r = threadIdx.x; r < rows; r += 256) {
-                const double w = W[r + (int64_t)c * ld];
-                a += w * w;
-            }
-        snorm[threadIdx.x] = a;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) snorm[threadIdx.x] += snorm[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const float sy = pow2_below(16384.0f, xmaxnorm * (float)sqrt(snorm[0]));
-            tcs[2 + c] = sy;
-            tcs[2 + PP + c] = 1.0f / (xscale * sy);
-        }
-        __syncthreads();
     }
 }
 
@@ -759,7 +766,9 @@ void y_hilo(cudaStream_t s, const float *Y, int64_t n, int PP, __nv_bfloat16 *Yb
 
 void pack_hilo_f16(cudaStream_t s, const float *W, int64_t ld, int64_t rows, int p, int PP, float xscale,
                    double xmaxnorm, float *tcs, __half *Wb) {
-    tc_scales_kernel<<<1, 256, 0, s>>>(W, ld, rows, p, PP, xscale, (float)xmaxnorm, tcs);
+    tc_colstats_kernel<<<(unsigned)PP, 256, 0, s>>>(W, ld, rows, p, PP, xscale, (float)xmaxnorm, tcs);
+    LRA_LAUNCHED();
+    tc_sw_kernel<<<1, 32, 0, s>>>(PP, xscale, tcs);
     LRA_LAUNCHED();
     pack_hilo_f16_kernel<<<(unsigned)ceil_div(rows * PP, 256), 256, 0, s>>>(W, ld, rows, p, PP, tcs, Wb);
     LRA_LAUNCHED();
