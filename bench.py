@@ -101,16 +101,17 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
-def recorded_traffic(workload, kernel):
-    """DRAM bytes per launch of `kernel` on `workload` from profiles/dram_traffic.txt
-    (an ncu capture of the current kernel), or None."""
+def recorded_traffic(workload, storage, kernel):
+    """DRAM bytes per launch of `kernel` on `workload` in `storage` from
+    profiles/dram_traffic.txt (an ncu capture of the current kernel), or None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(path) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) == 3 and not line.startswith("#") and parts[0] == workload and parts[1] == kernel:
-                    return int(parts[2])
+                if (len(parts) == 4 and not line.startswith("#") and parts[0] == workload and parts[1] == storage
+                        and parts[2] == kernel):
+                    return int(parts[3])
     except OSError:
         pass
     return None
@@ -560,7 +561,7 @@ def kernel_table(reps, src, storage, wl, peaks, peak_kind, workload):
             roof = {"bound": "hbm", "achieved": bytes_l / t_l / 1e9, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": bytes_l / t_l / hbm, "traffic": None}
         kname = KERNEL_NAMES[(dom, src.tensor)]
-        roof["traffic"] = recorded_traffic(workload, kname)
+        roof["traffic"] = recorded_traffic(workload, storage, kname)
         roof.update({"kernel": kname, "launches": cnt[dom], "ms_per_launch": t_l * 1e3,
                      "algorithmic_bytes_per_launch": bytes_l, "x_pass_gbs": bytes_l / t_l / 1e9,
                      "peak_source": peak_kind})
