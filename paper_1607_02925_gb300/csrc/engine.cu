@@ -280,7 +280,41 @@ void Engine::ensure_norms() {
     mat_->have_norms = true;
 }
 
+const lra_mat::Table &Engine::defl_table(int mode) {
+    auto &t = defl->table[mode];
+    if (t.ok) return t;
+    const int64_t n = mat_->n;
+    const int64_t scr = std::max<int64_t>(ceil_div(n, 1024) + 16, ceil_div(n, 256) + 16);
+    uint64_t *scratch = static_cast<uint64_t *>(dev_alloc(mat_->ctx, sizeof(uint64_t) * scr, s_));
+    try {
+        sampling_table(s_, defl->norm2, n, mode, defl->sm + 1, t.cum, t.c, defl->sm + 2, scratch);
+        uint64_t tot = 0;
+        double kp = 0;
+        LRA_CUDA(cudaMemcpyAsync(&tot, t.cum + n - 1, sizeof(tot), cudaMemcpyDeviceToHost, s_));
+        LRA_CUDA(cudaMemcpyAsync(&kp, defl->sm + 2, sizeof(kp), cudaMemcpyDeviceToHost, s_));
+        sync();
+        t.total = tot;
+        t.kappa = kp;
+        t.ok = true;
+    } catch (...) {
+        cudaStreamSynchronize(s_);
+        dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr, s_);
+        throw;
+    }
+    dev_free(mat_->ctx, scratch, sizeof(uint64_t) * scr, s_);
+    if (t.total == 0) {
+        set_error("the deflated X has no non-zero column");
+        throw Error{LRA_EINVAL};
+    }
+    return t;
+}
+
+void Engine::project(float *V, int p) {
+    if (defl && defl->c > 0) defl_project(s_, defl->U, mat_->dpad, defl->c, V, mat_->dpad, mat_->dpad, p, defl->C);
+}
+
 const lra_mat::Table &Engine::ensure_table(int mode) {
+    if (defl) return defl_table(mode);
     ensure_norms();
     std::lock_guard<std::mutex> g(mat_->setup_mu);
     auto &t = mat_->table[mode];
@@ -328,6 +362,12 @@ void Engine::check_tc() {
 
 void Engine::xt_mul(const float *W, int p, float *Y, bool use32, bool keep_hilo) {
     const int PP = pad_p(p);
+    if (defl && defl->c > 0) {
+        // X'^T W = X^T (I - U U^T) W
+        LRA_CUDA(cudaMemcpyAsync(defl->V, W, sizeof(float) * mat_->dpad * p, cudaMemcpyDeviceToDevice, s_));
+        project(defl->V, p);
+        W = defl->V;
+    }
     if (mat_->sp) {
         pack_rm(s_, W, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
         if (timer) timer->begin(KernelTimer::XTW, p);
@@ -397,6 +437,7 @@ void Engine::x_mul(const float *Y, int p, float *G, bool use32) {
     xy_pass(Y, p, use32);
     anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
                     ws_.epi, nullptr, 0.0, gscale_);
+    project(G, p);  // X' Y = (I - U U^T) X Y
 }
 
 void Engine::a_apply(const float *W, int p, float *G) {
@@ -409,6 +450,7 @@ void Engine::a_apply(const float *W, int p, float *G) {
     }
     anchor_epilogue(s_, ws_.Gp, ws_.nch, mat_->dpad, pad_p(p), p, 0.0, nullptr, nullptr, G, nullptr,
                     ws_.epi, nullptr, 0.0, gscale_);
+    project(G, p);
 }
 
 void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M, const float *G0,
@@ -426,10 +468,22 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
         xt_mul(Wt, p, ws_.Y, false);
         xy_pass(ws_.Y, p, false);
     }
+    const float *colscale = G0 ? nullptr : gscale_;
     if (!G0) nch = ws_.nch;
+    if (!G0 && defl && defl->c > 0) {
+        // X' X'^T Wt = (I - U U^T) X X^T (I - U U^T) Wt: the partials summed,
+        // projected and handed to the epilogue as one chunk
+        anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, 0.0, nullptr, nullptr, defl->V, nullptr, ws_.epi, nullptr,
+                        0.0, colscale);
+        project(defl->V, p);
+        pack_rm(s_, defl->V, mat_->dpad, mat_->dpad, p, PP, defl->G0);
+        Gsrc = defl->G0;
+        nch = 1;
+        colscale = nullptr;
+    }
     if (timer) timer->begin(KernelTimer::EPI, p);
     anchor_epilogue(s_, Gsrc, nch, mat_->dpad, PP, p, lam, Wt, B, M, ws_.norms, ws_.epi, acc ? acc->Z : nullptr,
-                    acc ? acc->gamma : 0.0, G0 ? nullptr : gscale_);
+                    acc ? acc->gamma : 0.0, colscale);
     if (timer) timer->end();
     if (nM2 || nB2) {
         LRA_CUDA(cudaMemcpyAsync(ws_.host, ws_.norms, (acc ? 3 : 2) * sizeof(double), cudaMemcpyDeviceToHost, s_));
@@ -443,14 +497,43 @@ void Engine::anchor(const float *Wt, const float *B, int p, double lam, float *M
 
 void Engine::inner(float *W, const float *Wt, const float *M, int p, const int32_t *idx,
                    const float *cval, int64_t m, double eta, double lam, int batch) {
-    if (mat_->sp) {
+    const bool deflated = defl && defl->c > 0;
+    if (mat_->sp && !(deflated && defl->mcap > 0)) {
         // factored form: Mr = M row-major in Wr, Z in the G buffer (both free
         // between the anchor's epilogue and the next X pass)
         const int PP = pad_p(p);
         pack_rm(s_, M, mat_->dpad, mat_->dpad, p, PP, ws_.Wr);
+        InnerDefl id;
+        if (deflated) {
+            id.U = defl->U;
+            id.c = defl->c;
+            id.Gt = defl->Gt;
+            id.PPc = defl->PPc;
+            id.scratch = defl->lk;
+        }
         if (timer) timer->begin(KernelTimer::INNER, p);
         svrg_inner_csc(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->dpad, p, PP, W, Wt, ws_.Wr,
-                       ws_.Gp, ws_.dots, idx, cval, m, eta, lam, batch);
+                       ws_.Gp, ws_.dots, idx, cval, m, eta, lam, batch, deflated ? &id : nullptr);
+        if (timer) timer->end();
+        return;
+    }
+    if (deflated) {
+        // the sampled columns of X' = (I - U U^T) X, formed chunk by chunk from the
+        // exact FP32 values (dense X, or a CSR X with d small enough for the dense
+        // steps), then the same steps on them in sampling order
+        const int64_t per = std::max<int64_t>(1, defl->mcap / batch);
+        if (timer) timer->begin(KernelTimer::INNER, p);
+        for (int64_t t0 = 0; t0 < m; t0 += per) {
+            const int64_t mt = std::min(per, m - t0);
+            if (mat_->sp)
+                defl_gather_csc(s_, mat_->sp->colptr, mat_->sp->rowidx, mat_->sp->cval, mat_->dpad, idx + t0 * batch,
+                                mt * batch, defl->U, defl->c, defl->Gt, defl->PPc, defl->cols);
+            else
+                defl_gather(s_, mat_->X32, mat_->dpad, mat_->dpad, idx + t0 * batch, mt * batch, defl->U, defl->c,
+                            defl->Gt, defl->PPc, defl->cols);
+            svrg_inner(s_, defl->cols, LRA_F32, mat_->dpad, mat_->dpad, p, W, Wt, M, defl->iota, cval + t0 * batch,
+                       mt, (float)eta, (float)lam, batch, 1.0f);
+        }
         if (timer) timer->end();
         return;
     }
@@ -495,7 +578,7 @@ void Engine::ritz(const float *S, int p, bool use32, int passes, bool with_xq) {
     // the basis as the tensor-core pass used it: its BF16 pair for FP32 and BF16
     // storage; FP16 storage splits it into FP16 hi/lo of a power-of-two multiple,
     // whose sum is S to about 2^-22, so S itself is used there
-    const bool bf16_pair = tc(use32) && mat_->storage != LRA_F16;
+    const bool bf16_pair = tc(use32) && mat_->storage != LRA_F16 && !(defl && defl->c > 0);
     gram64(ws_.side, S, nullptr, nullptr, mat_->dpad, mat_->dpad, p, ws_.Gm, ws_.gscr2, bf16_pair);
     LRA_CUDA(cudaEventRecord(ws_.ev_join, ws_.side));
     xt_mul(S, p, ws_.Q, use32, with_xq);
@@ -974,7 +1057,7 @@ lra_status Engine::power_block(int b, double eps, double r_floor, uint64_t seed,
         if (ell > 0 && (st = qr_status()) != LRA_OK) return st;
         double sb = 0.0;
         for (int j = 0; j < b; ++j) sb += h[j];
-        E.push_back(mat_->fro2 - sb);
+        E.push_back(fro2() - sb);
         if (outer_stop(E, eps, ell, o.min_outer, r_floor)) break;
         if (ell >= o.max_outer) {
             status = LRA_ENOTCONV;
@@ -1014,7 +1097,7 @@ lra_status Engine::loop_d(int k, int p, double eps, uint64_t seed, double lam, d
         if (ell > 0 && (st = qr_status()) != LRA_OK) return st;  // the previous step's CholeskyQR2
         double sk = 0.0;
         for (int j = 0; j < k; ++j) sk += h[j];
-        E.push_back(mat_->fro2 - sk);
+        E.push_back(fro2() - sk);
         if (o.trace_E && (int)E.size() <= o.trace_cap) o.trace_E[E.size() - 1] = E.back();
         const double rf = r_floor >= 0.0 ? r_floor : theory_rate(lam, h, k, p);
         if (outer_stop(E, eps, ell, o.min_outer, rf)) break;

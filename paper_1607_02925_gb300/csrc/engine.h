@@ -196,6 +196,28 @@ struct Workspace {
 
 size_t workspace_bytes(int64_t dpad, int64_t n, int pmax, int64_t sp_items = -1);
 
+// Deflation applied on the fly (Algorithm 6, Sec. 3): a stage's matrix is
+// X' = (I - U U^T) X for the orthonormal columns U (dpad x c) of the earlier
+// stages.  The Engine of such a stage projects the small operand before each
+// X^T pass and the d x p result after each X pass, samples by the deflated
+// column norms, and feeds its inner loop the deflated columns x_i - U g_i.
+struct Deflation {
+    const float *U = nullptr;
+    int c = 0, PPc = 0;
+    const float *Gt = nullptr;  // n x PPc row-major: row i = g_i = U^T x_i
+    double *norm2 = nullptr;    // n: ||x_i||^2 - ||g_i||^2
+    double *sm = nullptr;       // device [sum, max, kappa]
+    double fro2 = 0.0, maxn = 0.0;
+    lra_mat::Table table[2];
+    float *V = nullptr;         // dpad x pmax: a projected block
+    float *C = nullptr;         // c x pmax coefficients U^T V
+    float *G0 = nullptr;        // dpad x PPmax row-major: projected X X^T W of an anchor
+    float *cols = nullptr;      // dense X: deflated sampled columns, dpad x mcap
+    int64_t mcap = 0;
+    int32_t *iota = nullptr;    // 0, 1, ..., mcap - 1
+    float *lk = nullptr;        // sparse X: 3 c PPmax floats of the inner loop
+};
+
 // Algorithm 6 with adaptive partitioning and deflation (partition.cu)
 lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t seed, const Opts &o, float *U,
                              double *ritz, lra_report *rep);
@@ -283,8 +305,11 @@ class Engine {
 
     void sync();
     void check_tc();  // raise if a tensor-core kernel reported a timed-out wait
+    // ||X||_F^2 of the matrix the engine works on (the deflated one under defl)
+    double fro2() const { return defl ? defl->fro2 : mat_->fro2; }
     Stats stats;
     KernelTimer *timer = nullptr;
+    Deflation *defl = nullptr;  // non-null: the engine works on (I - U U^T) X
     long long tc_wait_ = 0;  // pipeline wait limit of the tensor-core passes (0 = default)
     const float *gscale_ = nullptr;  // per-column factor of the last X Y pass's partials (FP16 storage)
 
@@ -298,6 +323,9 @@ class Engine {
     // G-partials of one X Y pass into ws.Gp; Y32 == nullptr means ws.Yb already holds Y
     void xy_pass(const float *Y32, int p, bool use32);
     const void *xptr(bool use32) const { return use32 ? (const void *)mat_->X32 : mat_->X; }
+    // V <- (I - U U^T) V for a dpad x p column-major block (no-op without defl)
+    void project(float *V, int p);
+    const lra_mat::Table &defl_table(int mode);
     lra_dtype xdt(bool use32) const { return use32 ? LRA_F32 : mat_->storage; }
     lra_mat *mat_;
     Workspace &ws_;

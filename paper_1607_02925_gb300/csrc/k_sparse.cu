@@ -456,6 +456,14 @@ int sm_count_sparse() {
 // and Z is rescaled (Z <- a Z, a <- 1) once a < 2^-30.  One CTA runs the
 // chain; warp w takes the entries w, w + 8, ... of the column, lanes the columns
 // of the block (row-major Z and M, PP wide).
+//
+// Deflated matrix (I - U U^T) X (Algorithm 6 on the fly; U orthonormal, c
+// columns): the step's column is x'_i = x_i - U g_i, g_i = U^T x_i.  With
+// W - Wt = a (Z - U K) + b M, x'_i is orthogonal to U, so
+//     r = a (x_i^T Z - g_i^T L) + b (x_i^T M - g_i^T N),  L = U^T Z, N = U^T M,
+// and the step adds (eta c / a') x_i r to Z and (eta c / a') g_i r to both L
+// and K: K = L - L0 throughout (L0 = U^T Z at the start).  L, L0 and N (c x PP)
+// stay in shared memory; K is written out for the final W.
 // ---------------------------------------------------------------------------
 __global__ void zdiff_kernel(const float *__restrict__ W, const float *__restrict__ Wt, int64_t dpad, int p, int PP,
                              float *__restrict__ Z) {
@@ -475,16 +483,25 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
                                                                 const float *__restrict__ Mr, float *__restrict__ Z,
                                                                 const int32_t *__restrict__ idx,
                                                                 const float *__restrict__ cvals, int64_t m, double eta,
-                                                                double lam, double *__restrict__ ab) {
+                                                                double lam, double *__restrict__ ab,
+                                                                const float *__restrict__ Gt, int c, int PPc,
+                                                                const float *__restrict__ LN, float *__restrict__ Kout) {
     constexpr int kPer = kColCap / (32 * kWarps);  // staged entries per thread
     __shared__ int32_t sr[2][kColCap];
     __shared__ float sv[2][kColCap];
     __shared__ float redz[kWarps][32 * NQ], redm[kWarps][32 * NQ];
     __shared__ float rv[32 * NQ];
+    extern __shared__ float dfs[];  // deflation: L, L0, N (c x PP each), g of two steps
+    float *Ls = dfs, *L0s = dfs + (size_t)c * PP, *Ns = dfs + 2 * (size_t)c * PP, *gs = dfs + 3 * (size_t)c * PP;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const double g = 1.0 - eta * lam;
     double a = 1.0, b = 0.0;
 
+    for (int e = tid; e < c * PP; e += blockDim.x) {
+        Ls[e] = L0s[e] = LN[e];
+        Ns[e] = LN[(size_t)c * PP + e];
+    }
+    for (int e = tid; e < c; e += blockDim.x) gs[e] = Gt[(int64_t)idx[0] * PPc + e];
     // column of step 0 into buffer 0
     int64_t lo = colptr[idx[0]], hi = colptr[idx[0] + 1];
     if (hi - lo <= kColCap) {
@@ -535,6 +552,18 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
                 }
             }
         }
+        const float *gc = gs + (size_t)cur * c;
+        for (int u = w; u < c; u += kWarps) {
+            const float ga = gc[u];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < PP) {
+                    sz[q] = fmaf(-ga, Ls[u * PP + j], sz[q]);
+                    sm[q] = fmaf(-ga, Ns[u * PP + j], sm[q]);
+                }
+            }
+        }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             redz[w][lane + 32 * q] = sz[q];
@@ -564,7 +593,15 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
                 if (j < PP) Z[r * PP + j] = fmaf(cv, rv[j], Z[r * PP + j]);
             }
         }
-        // stage the next column (the other buffer is no longer read)
+        for (int u = w; u < c; u += kWarps) {
+            const float cg = coef * gc[u];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < PP) Ls[u * PP + j] = fmaf(cg, rv[j], Ls[u * PP + j]);
+            }
+        }
+        // stage the next column and g (the other buffers are no longer read)
         if (t + 1 < m && hi1 - lo1 <= kColCap) {
 #pragma unroll
             for (int u = 0; u < kPer; ++u) {
@@ -575,11 +612,17 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
                 }
             }
         }
+        if (t + 1 < m)
+            for (int e = tid; e < c; e += blockDim.x) gs[(size_t)(cur ^ 1) * c + e] = Gt[(int64_t)idx[t + 1] * PPc + e];
         a = a1;
         if (a < 0x1p-30) {
             __syncthreads();
             const float af = (float)a;
             for (int64_t e = tid; e < dpad * PP; e += blockDim.x) Z[e] *= af;
+            for (int e = tid; e < c * PP; e += blockDim.x) {
+                Ls[e] *= af;
+                L0s[e] *= af;
+            }
             a = 1.0;
         }
         lo = lo1;
@@ -590,6 +633,7 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_kernel(const int64_t *_
         ab[0] = a;
         ab[1] = b;
     }
+    for (int e = tid; e < c * PP; e += blockDim.x) Kout[e] = Ls[e] - L0s[e];
 }
 
 // The same chain with a batch of nb > 1 samples per step (stochastic term
@@ -601,11 +645,19 @@ template <int NQ>
 __global__ void __launch_bounds__(32 * kWarps) inner_csc_batch_kernel(
     const int64_t *__restrict__ colptr, const int32_t *__restrict__ rowidx, const float *__restrict__ cval,
     int64_t dpad, int PP, const float *__restrict__ Mr, float *__restrict__ Z, const int32_t *__restrict__ idx,
-    const float *__restrict__ cvals, int64_t m, int nb, double eta, double lam, double *__restrict__ ab) {
+    const float *__restrict__ cvals, int64_t m, int nb, double eta, double lam, double *__restrict__ ab,
+    const float *__restrict__ Gt, int c, int PPc, const float *__restrict__ LN, float *__restrict__ Kout) {
     __shared__ float rv[16][32 * NQ];
+    extern __shared__ float dfs[];  // deflation: L, L0, N (c x PP each)
+    float *Ls = dfs, *L0s = dfs + (size_t)c * PP, *Ns = dfs + 2 * (size_t)c * PP;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const double g = 1.0 - eta * lam;
     double a = 1.0, b = 0.0;
+    for (int e = tid; e < c * PP; e += blockDim.x) {
+        Ls[e] = L0s[e] = LN[e];
+        Ns[e] = LN[(size_t)c * PP + e];
+    }
+    __syncthreads();
     for (int64_t t = 0; t < m; ++t) {
         for (int u = w; u < nb; u += kWarps) {
             const int64_t i = idx[t * nb + u];
@@ -623,6 +675,17 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_batch_kernel(
                     if (j < PP) {
                         sz[q] = fmaf(v, Z[r * PP + j], sz[q]);
                         sm[q] = fmaf(v, __ldg(Mr + r * PP + j), sm[q]);
+                    }
+                }
+            }
+            for (int e = 0; e < c; ++e) {
+                const float ge = Gt[i * PPc + e];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < PP) {
+                        sz[q] = fmaf(-ge, Ls[e * PP + j], sz[q]);
+                        sm[q] = fmaf(-ge, Ns[e * PP + j], sm[q]);
                     }
                 }
             }
@@ -645,12 +708,24 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_batch_kernel(
                     if (j < PP) Z[r * PP + j] = fmaf(cv, rv[u][j], Z[r * PP + j]);
                 }
             }
+            for (int e = w; e < c; e += kWarps) {
+                const float cg = coef * Gt[i * PPc + e];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < PP) Ls[e * PP + j] = fmaf(cg, rv[u][j], Ls[e * PP + j]);
+                }
+            }
             __syncthreads();
         }
         a = a1;
         if (a < 0x1p-30) {
             const float af = (float)a;
             for (int64_t e = tid; e < dpad * PP; e += blockDim.x) Z[e] *= af;
+            for (int e = tid; e < c * PP; e += blockDim.x) {
+                Ls[e] *= af;
+                L0s[e] *= af;
+            }
             a = 1.0;
             __syncthreads();
         }
@@ -659,15 +734,20 @@ __global__ void __launch_bounds__(32 * kWarps) inner_csc_batch_kernel(
         ab[0] = a;
         ab[1] = b;
     }
+    for (int e = tid; e < c * PP; e += blockDim.x) Kout[e] = Ls[e] - L0s[e];
 }
 
+// W = Wt + a (Z - U K) + b M  (c = 0: no deflation)
 __global__ void inner_final_kernel(const float *__restrict__ Wt, const float *__restrict__ Z,
                                    const float *__restrict__ Mr, const double *__restrict__ ab, int64_t dpad, int p,
-                                   int PP, float *__restrict__ W) {
+                                   int PP, const float *__restrict__ U, int c, const float *__restrict__ K,
+                                   float *__restrict__ W) {
     const float a = (float)ab[0], b = (float)ab[1];
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < dpad * p; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / dpad, r = e - j * dpad;
-        W[e] = Wt[e] + a * Z[r * PP + j] + b * Mr[r * PP + j];
+        float z = Z[r * PP + j];
+        for (int u = 0; u < c; ++u) z = fmaf(-U[r + (int64_t)u * dpad], K[(int64_t)u * PP + j], z);
+        W[e] = Wt[e] + a * z + b * Mr[r * PP + j];
     }
 }
 
@@ -768,7 +848,8 @@ void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const 
 
 void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
                     int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
-                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch) {
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch,
+                    const InnerDefl *defl) {
     if (m <= 0) return;
     if (batch < 1 || batch > 16) {
         set_error("batch must be in [1, 16]");
@@ -776,17 +857,34 @@ void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx
     }
     zdiff_kernel<<<grid_for(dpad * PP, 256), 256, 0, s>>>(W, Wt, dpad, p, PP, Z);
     LRA_LAUNCHED();
+    const int c = defl ? defl->c : 0;
+    float *LN = defl ? defl->scratch : nullptr;  // L0 = U^T Z, N = U^T M, then K
+    float *K = LN ? LN + 2 * (size_t)c * PP : nullptr;
+    if (c > 0) {
+        defl_coef(s, defl->U, dpad, c, Z, PP, 1, dpad, PP, LN, PP);
+        defl_coef(s, defl->U, dpad, c, Mr, PP, 1, dpad, PP, LN + (size_t)c * PP, PP);
+    }
+    const float *Gt = defl ? defl->Gt : nullptr;
+    const int PPc = defl ? defl->PPc : 0;
     dispatch_nq(PP, [&](auto nq) {
         constexpr int NQ = decltype(nq)::value;
-        if (batch == 1)
-            inner_csc_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, eta,
-                                                           lam, ab);
-        else
-            inner_csc_batch_kernel<NQ><<<1, 32 * kWarps, 0, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m,
-                                                                 batch, eta, lam, ab);
+        if (batch == 1) {
+            auto k = inner_csc_kernel<NQ>;
+            const size_t smem = sizeof(float) * (3 * (size_t)c * PP + 2 * (size_t)c);
+            ensure_smem(k, (int)smem);
+            k<<<1, 32 * kWarps, smem, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, eta, lam, ab, Gt, c,
+                                           PPc, LN, K);
+        } else {
+            auto k = inner_csc_batch_kernel<NQ>;
+            const size_t smem = sizeof(float) * 3 * (size_t)c * PP;
+            ensure_smem(k, (int)smem);
+            k<<<1, 32 * kWarps, smem, s>>>(colptr, rowidx, cval, dpad, PP, Mr, Z, idx, cvals, m, batch, eta, lam, ab,
+                                           Gt, c, PPc, LN, K);
+        }
         LRA_LAUNCHED();
     });
-    inner_final_kernel<<<grid_for(dpad * p, 256), 256, 0, s>>>(Wt, Z, Mr, ab, dpad, p, PP, W);
+    inner_final_kernel<<<grid_for(dpad * p, 256), 256, 0, s>>>(Wt, Z, Mr, ab, dpad, p, PP, c > 0 ? defl->U : nullptr,
+                                                                c, K, W);
     LRA_LAUNCHED();
 }
 

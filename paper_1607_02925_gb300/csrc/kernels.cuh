@@ -177,10 +177,40 @@ void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const
 void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,
             int64_t dpad, const int64_t *item_off, const int2 *items, int64_t nitems, int seg, const float *Y,
             int PP, int p, float *G, float *partial);
+// Deflated columns x'_i = x_i - U g_i of the sparse inner loop: U dpad x c
+// column-major (orthonormal), Gt n x PPc row-major with g_i in row i, scratch
+// >= 3 c PP floats.
+struct InnerDefl {
+    const float *U = nullptr;
+    int c = 0;
+    const float *Gt = nullptr;
+    int PPc = 0;
+    float *scratch = nullptr;
+};
 // m inner steps in factored form: W (dpad x p col-major) from W = Wt + (W - Wt);
-// Mr = M packed dpad x PP row-major; Z: dpad x PP scratch; ab: 2 doubles
+// Mr = M packed dpad x PP row-major; Z: dpad x PP scratch; ab: 2 doubles.
+// defl != nullptr: the steps of the deflated matrix (I - U U^T) X
 void svrg_inner_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
                     int p, int PP, float *W, const float *Wt, const float *Mr, float *Z, double *ab,
-                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch = 1);
+                    const int32_t *idx, const float *cvals, int64_t m, double eta, double lam, int batch = 1,
+                    const InnerDefl *defl = nullptr);
+
+// ---- deflation applied on the fly (k_deflate.cu) -------------------------
+// C (c x p; row a at C + a ldc) = U^T V for U rows x c column-major (leading
+// dim ldu) and V[r rs + j cs]; FP32 products summed in FP64
+void defl_coef(cudaStream_t s, const float *U, int64_t ldu, int c, const float *V, int64_t rs, int64_t cs,
+               int64_t rows, int p, float *C, int ldc);
+// V <- V - U (U^T V) for V rows x p column-major (leading dim ldv); C: c x p scratch
+void defl_project(cudaStream_t s, const float *U, int64_t ldu, int c, float *V, int64_t ldv, int64_t rows, int p,
+                  float *C);
+// out[i] = max(0, norm2[i] - sum_{a < c} Gt[i PPc + a]^2)
+void defl_norms(cudaStream_t s, const double *norm2, const float *Gt, int PPc, int c, int64_t n, double *out);
+// out[:, t] = X[:, idx[t]] - U g_{idx[t]} for t < m (X FP32 dpad x n column-major
+// with leading dim ldx, U dpad x c, out FP32 dpad x m column-major)
+void defl_gather(cudaStream_t s, const float *X, int64_t ldx, int64_t dpad, const int32_t *idx, int64_t m,
+                 const float *U, int c, const float *Gt, int PPc, float *out);
+// the same for a sparse X given by its compressed columns
+void defl_gather_csc(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t dpad,
+                     const int32_t *idx, int64_t m, const float *U, int c, const float *Gt, int PPc, float *out);
 
 }  // namespace lra

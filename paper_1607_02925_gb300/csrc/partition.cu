@@ -1,9 +1,12 @@
 // Algorithm 6 with adaptive partitioning of {1..k} and deflation (Sec. 3:
 // Algorithms 3, 4, 5, 6, 7).  Stage t, starting at index s with the columns
 // u_1..u_{s-1} found so far, works on the deflated matrix
-// X_{-(s-1)} = (I - U U^T) X, formed explicitly (Sec. 3 assumes the projection
-// already applied to X's columns) as a dense matrix of the original storage,
-// so that every stage runs the same kernels as the q = k path:
+// X_{-(s-1)} = (I - U U^T) X (Sec. 3 assumes the projection applied to X's
+// columns).  It is applied on the fly: the stage's Engine projects the small
+// operand before each X^T pass and the d x p result after each X pass, draws
+// samples by the deflated column norms ||x_i||^2 - ||U^T x_i||^2, and steps on
+// the deflated columns x_i - U (U^T x_i); no d x n copy is made.  Each stage
+// runs the same kernels as the q = k path:
 //   Algorithm 3 on A_{-(s-1)} (k - s + 1 vectors, eps' = 1/(9 p^2));
 //   Algorithm 4: the first multiplicative gap -> Algorithm 1 on A_{-(s-1)}
 //   with q - s + 1 columns; otherwise Algorithm 7 (the shift), Algorithm 3 on
@@ -23,80 +26,6 @@
 namespace lra {
 
 namespace {
-
-constexpr int kDT = 32;  // deflation tile: 32 rows x 32 columns
-
-// out[r + i ldo] = X[r + i ldx] - sum_a U[r + a ldu] Y[i PP + a] for r < rows,
-// i < n (X == nullptr: 0 - ...); U is column-major, Y = X^T U row-major n x PP.
-template <typename TX>
-__global__ void __launch_bounds__(256) deflate_kernel(const TX *__restrict__ X, int64_t ldx,
-                                                      const float *__restrict__ U, int64_t ldu, int c,
-                                                      const float *__restrict__ Y, int PP, int64_t rows,
-                                                      int64_t n, float *__restrict__ out, int64_t ldo) {
-    extern __shared__ float dsm[];
-    const int cs = c + 1;
-    float *Us = dsm, *Ys = dsm + kDT * cs;
-    const int64_t i0 = (int64_t)blockIdx.x * kDT, r0 = (int64_t)blockIdx.y * kDT;
-    for (int e = threadIdx.x; e < kDT * c; e += 256) {
-        const int rr = e % kDT, a = e / kDT;
-        const int64_t r = r0 + rr;
-        Us[rr * cs + a] = r < rows ? U[r + (int64_t)a * ldu] : 0.0f;
-    }
-    for (int e = threadIdx.x; e < kDT * c; e += 256) {
-        const int a = e % c, ii = e / c;
-        const int64_t i = i0 + ii;
-        Ys[ii * cs + a] = i < n ? Y[i * PP + a] : 0.0f;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t r = r0 + tx;
-    if (r >= rows) return;
-    for (int jj = 0; jj < kDT / 8; ++jj) {
-        const int ii = ty * (kDT / 8) + jj;
-        const int64_t i = i0 + ii;
-        if (i >= n) break;
-        float acc = 0.0f;
-        for (int a = 0; a < c; ++a) acc = fmaf(Us[tx * cs + a], Ys[ii * cs + a], acc);
-        const float x = X ? to_f32(X[r + i * ldx]) : 0.0f;
-        out[r + i * ldo] = x - acc;
-    }
-}
-
-// out[rowidx[e] + i ldo] += val[e] for the entries e of compressed column i
-__global__ void csc_add_kernel(const int64_t *__restrict__ colptr, const int32_t *__restrict__ rowidx,
-                               const float *__restrict__ val, int64_t n, float *__restrict__ out, int64_t ldo) {
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= n) return;
-    for (int64_t e = colptr[i] + (threadIdx.x & 31); e < colptr[i + 1]; e += 32)
-        out[rowidx[e] + i * ldo] += val[e];
-}
-
-void deflate(cudaStream_t s, const lra_mat *m, const float *U, int c, const float *Y, int PP, float *out) {
-    const int64_t rows = m->dpad, n = m->n;
-    const dim3 grid((unsigned)ceil_div(n, kDT), (unsigned)ceil_div(rows, kDT));
-    const size_t smem = sizeof(float) * 2 * kDT * (c + 1);
-    if (m->sp) {
-        deflate_kernel<float><<<grid, 256, smem, s>>>(nullptr, 0, U, rows, c, Y, PP, rows, n, out, rows);
-        LRA_LAUNCHED();
-        csc_add_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(m->sp->colptr, m->sp->rowidx, m->sp->cval, n, out,
-                                                               rows);
-        LRA_LAUNCHED();
-    } else if (m->storage == LRA_BF16) {
-        deflate_kernel<__nv_bfloat16><<<grid, 256, smem, s>>>(static_cast<const __nv_bfloat16 *>(m->X), rows, U,
-                                                              rows, c, Y, PP, rows, n, out, rows);
-        LRA_LAUNCHED();
-    } else {
-        deflate_kernel<float><<<grid, 256, smem, s>>>(m->X32, rows, U, rows, c, Y, PP, rows, n, out, rows);
-        LRA_LAUNCHED();
-    }
-}
-
-struct MatGuard {
-    lra_mat *m = nullptr;
-    ~MatGuard() {
-        if (m) lra_mat_destroy(m);
-    }
-};
 
 // Algorithm 4: offset j of the first q = s + j in I \ {k} with
 // lam_hat[j + 1] <= lam_hat[j] (1 - p^-2), or -1
@@ -155,6 +84,44 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
     float *Ucols = static_cast<float *>(ubuf.p);
     LRA_CUDA(cudaMemsetAsync(Ucols, 0, sizeof(float) * dpad * p, s));
 
+    // the deflation view of the stages after the first: U^T x_i (in ws0.Y, n x
+    // pad_p(c)), the deflated norms and sampling tables, projection scratch,
+    // and the inner loop's deflated columns in chunks of up to 256 MB (dense X,
+    // and CSR X up to d = 8192, where the dense steps are faster than the
+    // factored ones; larger CSR X steps in factored form)
+    const int PPp = pad_p(p);
+    const int64_t mcap =
+        (mat->sp && dpad > 8192)
+            ? 0
+            : std::max<int64_t>(64, std::min<int64_t>(65536, (int64_t)((256ull << 20) / (sizeof(float) * dpad))));
+    Buf bn(ctx, sizeof(double) * n), bsm(ctx, sizeof(double) * 4), bV(ctx, sizeof(float) * dpad * p),
+        bC(ctx, sizeof(float) * (size_t)p * p), bG0(ctx, sizeof(float) * dpad * PPp),
+        bcum0(ctx, sizeof(uint64_t) * n), bc0(ctx, sizeof(float) * n), bcum1(ctx, sizeof(uint64_t) * n),
+        bc1(ctx, sizeof(float) * n), bcols(ctx, sizeof(float) * dpad * std::max<int64_t>(mcap, 1)),
+        biota(ctx, sizeof(int32_t) * std::max<int64_t>(mcap, 1)), blk(ctx, sizeof(float) * 3 * (size_t)p * PPp);
+    Deflation D;
+    D.U = Ucols;
+    D.Gt = ws0.Y;
+    D.norm2 = static_cast<double *>(bn.p);
+    D.sm = static_cast<double *>(bsm.p);
+    D.V = static_cast<float *>(bV.p);
+    D.C = static_cast<float *>(bC.p);
+    D.G0 = static_cast<float *>(bG0.p);
+    D.table[0].cum = static_cast<uint64_t *>(bcum0.p);
+    D.table[0].c = static_cast<float *>(bc0.p);
+    D.table[1].cum = static_cast<uint64_t *>(bcum1.p);
+    D.table[1].c = static_cast<float *>(bc1.p);
+    D.cols = static_cast<float *>(bcols.p);
+    D.mcap = mcap;
+    D.iota = static_cast<int32_t *>(biota.p);
+    D.lk = static_cast<float *>(blk.p);
+    if (mcap > 0) {
+        std::vector<int32_t> iota((size_t)mcap);
+        for (int64_t i = 0; i < mcap; ++i) iota[(size_t)i] = (int32_t)i;
+        LRA_CUDA(cudaMemcpyAsync(D.iota, iota.data(), sizeof(int32_t) * mcap, cudaMemcpyHostToDevice, s));
+        LRA_CUDA(cudaStreamSynchronize(s));
+    }
+
     lra_status status = LRA_OK;
     int s_idx = 1, t = 0, ncols = 0;
     std::vector<double> lam_hat(k + 1), theta(k + 1), inv(k + 1);
@@ -162,26 +129,24 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
         ++t;
         const uint64_t seed_t = stream_key(seed, LRA_STREAM_PART, (uint64_t)t, 0);
         const int kk = k - s_idx + 1;
-        MatGuard defl;
-        lra_mat *cur = mat;
         if (s_idx > 1) {
-            // X_{-(s-1)} = X - U (X^T U)^T, then a matrix of the original storage
-            const int PP = pad_p(ncols);
-            e0.xt_mul(Ucols, ncols, ws0.Y, false);
-            lra_status st;
-            {
-                Buf tmp(ctx, sizeof(float) * dpad * n);
-                deflate(s, mat, Ucols, ncols, ws0.Y, PP, static_cast<float *>(tmp.p));
-                LRA_CUDA(cudaStreamSynchronize(s));
-                const lra_dtype storage = mat->sp ? LRA_F32 : mat->storage;
-                st = lra_create_dense(ctx, d, n, LRA_F32, tmp.p, dpad, 1, storage, &defl.m);
-            }
-            if (st != LRA_OK) return st;
-            cur = defl.m;
+            // g_i = U^T x_i from the exact FP32 values, then the deflated norms
+            D.c = ncols;
+            D.PPc = pad_p(ncols);
+            e0.xt_mul(Ucols, ncols, ws0.Y, true);
+            defl_norms(s, mat->norm2, D.Gt, D.PPc, D.c, n, D.norm2);
+            sum_max(s, D.norm2, n, D.sm, nullptr);
+            double h[2];
+            LRA_CUDA(cudaMemcpyAsync(h, D.sm, sizeof(h), cudaMemcpyDeviceToHost, s));
+            LRA_CUDA(cudaStreamSynchronize(s));
+            D.fro2 = h[0];
+            D.maxn = h[1];
+            D.table[0].ok = D.table[1].ok = false;
         }
-        Workspace ws(ctx, cur->dpad, cur->n, p, nullptr, ws_items(cur));
-        Engine e(cur, ws, s);
+        Workspace ws(ctx, dpad, n, p, nullptr, ws_items(mat));
+        Engine e(mat, ws, s);
         e.timer = timer.get();
+        if (s_idx > 1) e.defl = &D;
         e.ensure_table(o.sampling);
         int it3 = 0;
         lra_status st = e.alg3_a(kk, 1.0 / (9.0 * p * p), o.part_max_iters, seed_t, lam_hat.data(), it3);
@@ -225,7 +190,7 @@ lra_status solve_partitioned(lra_mat *mat, int k, int p, double eps, uint64_t se
             if (st != LRA_OK) return st;
             // Ritz vectors S V[:, :keep] into ws.U
             evecs_to_rm(s, ws.evecs, pp, keep, ws.P);
-            apply_right(s, S, cur->dpad, 1, cur->dpad, pp, ws.P, keep, ws.U, 1, cur->dpad);
+            apply_right(s, S, dpad, 1, dpad, pp, ws.P, keep, ws.U, 1, dpad);
             cols = ws.U;
             R.shift_rounds += rounds;
             R.lambda = lam;

@@ -1,5 +1,6 @@
 """Algorithm 6 with adaptive partitioning and deflation (lra_options.partition)
-against the FP64 oracle's adaptive_solve (needs a GPU).
+against the FP64 oracle's adaptive_solve (needs a GPU).  The library applies
+the deflation on the fly; the oracle forms the deflated matrix.
 
 The stage decisions (which q each stage finds, and by which branch) are
 integers taken from estimates with wide margins on the planted workload, so
@@ -92,6 +93,32 @@ def test_partition_on_csr_input(ctx):
         assert stages(rep) == [(1, 1), (3, 2)]
         ratio = O.frobenius_error(Xs, cm(Ud)) / opt
         assert 1.0 - 1e-6 <= ratio <= 1.0 + 1e-3
+    finally:
+        lra.lra_mat_destroy(m)
+
+
+def test_partition_on_csr_input_beyond_the_dense_inner_limit(ctx):
+    """d = 20000, above the dense inner loop's reach: the deflated stages step
+    in the CSR kernels' factored form with the projection applied on the fly (no
+    d x n copy of the deflated matrix is formed).  lambda_1 is far above lambda_2 (a
+    multiplicative gap at 1), so a second, deflated stage follows the first."""
+    d, n, k, p = 20000, 6000, 3, 6
+    rowptr, colidx, val = L.zipf_csr(d, n, 43, mean_nnz=20.0)
+    Xs = sp.csr_matrix((val, colidx, rowptr), shape=(d, n)).T.tocsr()
+    lam = O.top_eigs_lanczos(Xs, p + 1)
+    assert lam[1] < lam[0] * (1 - 1.0 / p ** 2)
+    opt = O.colnorms(Xs)[1] - float(lam[:k].sum())
+    m = lra.lra_create_csr(ctx, d, n, int(rowptr[-1]), rowptr, colidx, val, False)
+    try:
+        Ud = torch.zeros(k, d, dtype=torch.float32, device=DEV)
+        ritz = torch.zeros(k, dtype=torch.float64, device=DEV)
+        rep = lra.LraReport()
+        st = lra.lra_solve(m, k, p, 1e-3, 5, lra.options(partition=1, acc=1, part_max_iters=30), Ud, ritz, rep)
+        assert st == 0
+        assert rep.part_stages >= 2 and stages(rep)[0] == (1, 1)
+        ratio = O.frobenius_error(Xs, cm(Ud)) / opt
+        assert 1.0 - 1e-6 <= ratio <= 1.0 + 1e-3
+        assert np.allclose(ritz.cpu().numpy(), lam[:k], rtol=1e-3)
     finally:
         lra.lra_mat_destroy(m)
 
