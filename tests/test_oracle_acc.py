@@ -79,10 +79,11 @@ def test_outer_residual_from_the_first_anchor():
     assert st.outer_res == pytest.approx(direct, rel=1e-12)
 
 
-def _exact_run(Xt, A, B, lam, mu, gamma_target, S, beta_zero=False, check_outer=True):
-    """acc_svrg_solve with exact subproblem solves, S iterations, no stop."""
+def _exact_run(Xt, A, B, lam, mu, gamma_target, S, beta_zero=False):
+    """acc_svrg_solve with exact subproblem solves and exactly S iterations
+    (fixed_epochs > 0 turns the residual and stall stops off)."""
     d = A.shape[0]
-    ctx = O.Context(Xt, 0, O.Options(tau=0.0, acc_max_outer=S, acc_target=gamma_target))
+    ctx = O.Context(Xt, 0, O.Options(tau=0.0, acc_max_outer=S, acc_target=gamma_target, fixed_epochs=1))
 
     def exact(R, W, lam_p, mu_p):
         return np.linalg.solve(lam_p * np.eye(d) - A, R)
@@ -95,7 +96,7 @@ def _exact_run(Xt, A, B, lam, mu, gamma_target, S, beta_zero=False, check_outer=
             W = exact(B + g * W, W, lam + g, mu + g)
         return W, g
     W, st = ctx.acc_svrg_solve(B, np.zeros_like(B), lam, mu, lam / 1.0, inner=exact)
-    assert st.outer == S or not check_outer
+    assert st.outer == S
     return W, ctx.acc_gamma(lam, mu, lam / 1.0)
 
 
@@ -148,10 +149,10 @@ def test_wrong_momentum_is_caught(monkeypatch):
     monkeypatch.setattr(O, "math", FlippedMath())
     _, g = _exact_run(Xt, A, B, lam, mu, 40, 1)
     q = mu / (mu + g)
-    # (the stall stop may end the broken loop early; its error still shows)
-    W, _ = _exact_run(Xt, A, B, lam, mu, 40, 60, check_outer=False)
+    # 25 iterations exactly, as in the rate test above
+    W, _ = _exact_run(Xt, A, B, lam, mu, 40, 25)
     err = np.linalg.norm(W - Wstar) / np.linalg.norm(Wstar)
-    assert not err <= 2.0 * 61 * (1.0 - real_sqrt(q)) ** 60
+    assert not err <= 2.0 * 26 * (1.0 - real_sqrt(q)) ** 25
 
 
 def test_accelerated_solve_reaches_the_residual():
