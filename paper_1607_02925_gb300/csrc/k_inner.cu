@@ -381,9 +381,11 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[NP], int lane) {
 }
 
 // Block totals of NV values over NW <= 16 warps: warp totals by the
-// transposing butterfly, one shared row of 16 per value, every thread sums the
-// warps' entries in a fixed order from NW / 4 16-byte loads (entries of absent
-// warps hold zeros).
+// transposing butterfly, one shared row of 16 per value; then NW lanes per
+// value read its warps' entries and sum them by an xor butterfly, and every
+// lane takes the totals by shuffles.  The tree is fixed (pairs, then pairs of
+// pairs), so the result does not depend on timing; entries of absent warps
+// hold zeros.
 template <int NV, int NP, int NW>
 __device__ __forceinline__ void block_sum16(float (&v)[NP], float (*red)[16], int lane, int warp) {
     constexpr int LB = 5 - (NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : NP == 16 ? 4 : 5);
@@ -391,17 +393,21 @@ __device__ __forceinline__ void block_sum16(float (&v)[NP], float (*red)[16], in
     const int idx = lane >> LB;
     if ((lane & ((1 << LB) - 1)) == 0 && idx < NV) red[idx][warp] = w;
     __syncthreads();
+    constexpr int G = NW <= 2 ? 2 : NW <= 4 ? 4 : NW <= 8 ? 8 : 16;  // lanes per value
+    constexpr int VPR = 32 / G;                                       // values per round
+    constexpr int RND = (NV + VPR - 1) / VPR;
+    float part[RND];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const float4 *q = reinterpret_cast<const float4 *>(red[i]);
-        const float4 a = q[0], b = q[1];
-        float t = ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w));
-        if constexpr (NW > 8) {
-            const float4 c = q[2], d = q[3];
-            t = t + (((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w)));
-        }
-        v[i] = t;
+    for (int rr = 0; rr < RND; ++rr) {
+        const int i = rr * VPR + lane / G;
+        part[rr] = i < NV ? red[i][lane % G] : 0.0f;
     }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+        for (int rr = 0; rr < RND; ++rr) part[rr] += __shfl_xor_sync(0xffffffffu, part[rr], o);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = __shfl_sync(0xffffffffu, part[i / VPR], (i % VPR) * G);
 }
 
 // Ring depth of the look-ahead kernel: the deepest of 8, 6, 4, 3 columns of
@@ -416,7 +422,7 @@ template <int NV>
 __host__ __device__ constexpr int pow2_at_least() { return NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32; }
 
 template <typename TX, int S, int PC, int NW, int R = la_ring<TX, S>()>
-__global__ void __launch_bounds__(512) svrg_inner_la_kernel(
+__global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
     const TX *__restrict__ X, int64_t ldx, int64_t dpad, int p, float *__restrict__ W,
     const float *__restrict__ Wt, const float *__restrict__ M, const int32_t *__restrict__ idx,
     const float *__restrict__ cval, int64_t m, float eta, float lam,
@@ -454,24 +460,28 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
         }
     }
 
-    auto prefetch = [&](int64_t t) {
+    // rows of this thread and ring slots in 32-bit arithmetic (dpad <= 8192 here);
+    // column t sits in slot t mod R
+    const int dp = (int)dpad;
+    int rofs[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) rofs[s] = 4 * (tid + s * NT);
+    auto prefetch = [&](int64_t t, int slot) {
         if (t < m) {
             const TX *col = X + (int64_t)idx[t] * ldx;
-            TX *slot = ring + (t % R) * dpad;
+            TX *dst = ring + slot * dp;
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
-                if (r < dpad) cp_async_bytes<BYTES>(slot + r, col + r);
-            }
+            for (int s = 0; s < S; ++s)
+                if (rofs[s] < dp) cp_async_bytes<BYTES>(dst + rofs[s], col + rofs[s]);
         }
         cp_async_commit();
     };
-    auto load = [&](int64_t t, float2 (&x)[S][2]) {
-        const TX *slot = ring + (t % R) * dpad;
+    auto load = [&](int64_t t, int slot_i, float2 (&x)[S][2]) {
+        const TX *slot = ring + slot_i * dp;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const int64_t r = 4 * ((int64_t)tid + (int64_t)s * NT);
-            if (t < m && r < dpad) {
+            const int r = rofs[s];
+            if (t < m && r < dp) {
                 float q[4];
                 load4_f32(slot + r, q);
                 x[s][0] = make_float2(q[0], q[1]);
@@ -519,11 +529,11 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
     };
 
 #pragma unroll
-    for (int u = 0; u < R - 1; ++u) prefetch(u);
+    for (int u = 0; u < R - 1; ++u) prefetch(u, u);
     float2 x0[S][2], x1[S][2], x2[S][2];
     float r[PC];
     cp_async_wait<R - 2>();
-    load(0, x0);
+    load(0, 0, x0);
     {
         constexpr int NP0 = pow2_at_least<PC>();
         float v0[NP0];
@@ -542,13 +552,20 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
 #pragma unroll
         for (int j = 0; j < PC; ++j) r[j] = v0[j];
     }
-    int buf = 0;
-    for (int64_t t = 0; t < m; t += 2, buf ^= 1) {
-        prefetch(t + R - 1);
-        prefetch(t + R);
+    int s0 = 0;  // t mod R
+    // two steps from column t in xa (columns t + 1, t + 2 loaded into xb, xc);
+    // the loop alternates the roles of x0 and x2 instead of copying x2 to x0
+    auto two_steps = [&](int64_t t, float2 (&xa)[S][2], float2 (&xb)[S][2], float2 (&xc)[S][2],
+                         float (*redb)[16]) {
+        const int sm1 = s0 == 0 ? R - 1 : s0 - 1;
+        const int sp1 = s0 + 1 >= R ? s0 + 1 - R : s0 + 1;
+        const int sp2 = s0 + 2 >= R ? s0 + 2 - R : s0 + 2;
+        prefetch(t + R - 1, sm1);
+        prefetch(t + R, s0);
         cp_async_wait<R - 2>();
-        load(t + 1, x1);
-        load(t + 2, x2);
+        load(t + 1, sp1, xb);
+        load(t + 2, sp2, xc);
+        s0 = sp2;
         const float c0 = etac * cval[t];
         const float c1v = (t + 1 < m) ? etac * cval[t + 1] : 0.0f;
         float ct[PC];
@@ -558,26 +575,26 @@ __global__ void __launch_bounds__(512) svrg_inner_la_kernel(
 #pragma unroll
         for (int i = NV; i < NP; ++i) acc[i] = 0.0f;
         // chain A: r_{t+1} from Delta_t
-        dots(x1, x0, acc, acc + PC, acc[4 * PC]);
+        dots(xb, xa, acc, acc + PC, acc[4 * PC]);
         // step t
-        update(x0, ct);
+        update(xa, ct);
         // chain B: r_{t+2} from Delta_{t+1}, less the c_{t+1} term
-        dots(x2, x1, acc + 2 * PC, acc + 3 * PC, acc[4 * PC + 1]);
-        block_sum16<NV, NP, NW>(acc, red[buf], lane, warp);
+        dots(xc, xb, acc + 2 * PC, acc + 3 * PC, acc[4 * PC + 1]);
+        block_sum16<NV, NP, NW>(acc, redb, lane, warp);
         float c1[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) c1[j] = c1v * fmaf(a, acc[j], fmaf(ct[j], acc[4 * PC], -acc[PC + j]));
         if (t + 1 < m) {
             // step t + 1
-            update(x1, c1);
+            update(xb, c1);
 #pragma unroll
             for (int j = 0; j < PC; ++j)
                 r[j] = fmaf(a, acc[2 * PC + j], fmaf(c1[j], acc[4 * PC + 1], -acc[3 * PC + j]));
         }
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) x0[s][h] = x2[s][h];
+    };
+    for (int64_t t = 0; t < m; t += 4) {
+        two_steps(t, x0, x1, x2, red[0]);
+        if (t + 2 < m) two_steps(t + 2, x2, x1, x0, red[1]);
     }
     cp_async_wait<0>();
 

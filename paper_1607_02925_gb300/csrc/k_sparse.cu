@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(32 * kWarps) long_rows_kernel(const int64_t *_
 }
 
 // ---------------------------------------------------------------------------
-// Gather-accumulate with lane groups: GL lanes (a power of two, 4 GL >= p)
+// Gather-accumulate with power-of-two lane groups (the X Y pass): GL lanes (4 GL >= p)
 // take one entry, each lane a float4 of the gathered row, so 32 / GL entries
 // are in flight per warp instruction; entries lo + g, lo + g + 32/GL, ... go
 // to group g.  Rows below H come from the shared-memory copy `hot` (row
@@ -369,6 +369,91 @@ __device__ __forceinline__ void store_line4(float *__restrict__ dst, int PP, int
     if (lane < GL && 4 * lane < PP) *reinterpret_cast<float4 *>(dst + 4 * lane) = acc;
 }
 
+// ---------------------------------------------------------------------------
+// Gather-accumulate with exact-width lane groups (the X^T W pass; measured on
+// the 50000 x 500000 Zipf matrix at p = 20: 0.570 ms per pass against 0.674 ms
+// with power-of-two groups, while the X Y pass ran 0.802 against 0.612 ms in
+// this form and keeps the power-of-two one): gl = ceil(p / 4) lanes take one entry,
+// each lane a float4 of the gathered row, so ng = 32 / gl entries are in flight
+// per warp instruction (lanes gl ng .. 31 idle); entries lo + g, lo + g + ng, ...
+// go to group g.  Rows below H come from the shared-memory copy `hot` (row
+// stride p4 = 4 gl); the others from B (row-major, PP wide) through the
+// read-only path.  On return lane l < gl holds the sum over the groups of its
+// four columns, added in a fixed order (a butterfly when gl is a power of two,
+// else group by group), so results do not depend on timing.
+// ---------------------------------------------------------------------------
+struct LaneGroup {
+    int gl, ng, g, l;
+    __device__ LaneGroup(int p, int lane) {
+        gl = (p + 3) >> 2;
+        ng = 32 / gl;
+        g = lane / gl;
+        l = lane - g * gl;
+    }
+};
+
+__device__ __forceinline__ float4 gather_line(const int32_t *__restrict__ idx, const float *__restrict__ vals,
+                                              int64_t lo, int64_t hi, const float *__restrict__ B, int PP,
+                                              const float *hot, int H, const LaneGroup &lg, int lane) {
+    const bool active = lg.g < lg.ng;
+    const int p4 = 4 * lg.gl, l4 = 4 * lg.l;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // the (index, value) chunk of 32 entries is loaded one chunk ahead
+    int32_t rn = lo + lane < hi ? __ldg(idx + lo + lane) : 0;
+    float vn = lo + lane < hi ? __ldg(vals + lo + lane) : 0.0f;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int32_t rr = rn;
+        const float vv = vn;
+        const int64_t k = base + 32 + lane;
+        rn = k < hi ? __ldg(idx + k) : 0;
+        vn = k < hi ? __ldg(vals + k) : 0.0f;
+        const int cnt = (int)((hi - base) < 32 ? (hi - base) : 32);
+#pragma unroll 4
+        for (int e = 0; e < cnt; e += lg.ng) {
+            const int src = e + lg.g;
+            const int r = __shfl_sync(0xffffffffu, rr, src & 31);
+            const float v = __shfl_sync(0xffffffffu, vv, src & 31);
+            if (active && src < cnt) {
+                float4 b;
+                if (r < H)
+                    b = *reinterpret_cast<const float4 *>(hot + r * p4 + l4);
+                else
+                    b = __ldg(reinterpret_cast<const float4 *>(B + (int64_t)r * PP + l4));
+                acc.x = fmaf(v, b.x, acc.x);
+                acc.y = fmaf(v, b.y, acc.y);
+                acc.z = fmaf(v, b.z, acc.z);
+                acc.w = fmaf(v, b.w, acc.w);
+            }
+        }
+    }
+    if ((lg.gl & (lg.gl - 1)) == 0) {
+        // gl a power of two (ng gl = 32): butterfly over the group bits
+        for (int o = lg.gl; o < 32; o <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+        }
+        return acc;
+    }
+    float4 t = acc;
+    for (int gg = 1; gg < lg.ng; ++gg) {
+        const int from = (lg.l + gg * lg.gl) & 31;
+        t.x += __shfl_sync(0xffffffffu, acc.x, from);
+        t.y += __shfl_sync(0xffffffffu, acc.y, from);
+        t.z += __shfl_sync(0xffffffffu, acc.z, from);
+        t.w += __shfl_sync(0xffffffffu, acc.w, from);
+    }
+    return t;
+}
+
+// lanes l < PP / 4 store the PP-wide row: the group sum for l < gl, zeros beyond
+__device__ __forceinline__ void store_line(float *__restrict__ dst, int PP, int lane, const LaneGroup &lg,
+                                           float4 t) {
+    if (4 * lane < PP)
+        *reinterpret_cast<float4 *>(dst + 4 * lane) = lane < lg.gl ? t : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
 // Six CTAs of 256 threads per SM, each with 32 KB of hot rows (a sweep over
 // 0-200 KB of hot rows and 128-512 threads on the 50000 x 500000 Zipf matrix,
 // p = 20: 0.67 ms per pass here, 0.78 ms without hot rows, 1.30 ms with 200 KB
@@ -380,26 +465,26 @@ constexpr size_t kHotBytes = 32 * 1024;  // shared memory for the hot rows of W
 // Y (n x PP row-major) = X^T Wr: warp per column x_i.  The first H rows of
 // Wr (the most frequent row ids of a Zipf-like X come first) are copied to
 // shared memory once per CTA; kXtPerSm persistent CTAs per SM.
-template <int GL>
-__global__ void __launch_bounds__(kXtThreads) spmm_xt4_kernel(const int64_t *__restrict__ colptr,
-                                                             const int32_t *__restrict__ rowidx,
-                                                             const float *__restrict__ cval, int64_t n,
-                                                             const float *__restrict__ Wr, int PP, int p, int H,
-                                                             float *__restrict__ Y) {
+__global__ void __launch_bounds__(kXtThreads) spmm_xt_kernel(const int64_t *__restrict__ colptr,
+                                                            const int32_t *__restrict__ rowidx,
+                                                            const float *__restrict__ cval, int64_t n,
+                                                            const float *__restrict__ Wr, int PP, int p, int H,
+                                                            float *__restrict__ Y) {
     extern __shared__ float4 hot4[];
-    const int p4 = (p + 3) & ~3;
-    const int64_t nv = (int64_t)H * (p4 / 4);
+    const int lane = threadIdx.x & 31;
+    const LaneGroup lg(p, lane);
+    const int q4 = lg.gl;  // float4s per hot row
+    const int64_t nv = (int64_t)H * q4;
     for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
-        const int64_t row = e / (p4 / 4);
-        const int c = (int)(e - row * (p4 / 4)) * 4;
+        const int64_t row = e / q4;
+        const int c = (int)(e - row * q4) * 4;
         hot4[e] = *reinterpret_cast<const float4 *>(Wr + row * PP + c);
     }
     __syncthreads();
     const float *hot = reinterpret_cast<const float *>(hot4);
-    const int lane = threadIdx.x & 31;
     for (int64_t i = global_warp(); i < n; i += warps_in_grid()) {
-        const float4 acc = gather_line4<GL>(rowidx, cval, colptr[i], colptr[i + 1], Wr, PP, p, hot, H, p4, lane);
-        store_line4<GL>(Y + i * PP, PP, lane, acc);
+        const float4 t = gather_line(rowidx, cval, colptr[i], colptr[i + 1], Wr, PP, hot, H, lg, lane);
+        store_line(Y + i * PP, PP, lane, lg, t);
     }
 }
 
@@ -437,6 +522,13 @@ void dispatch_gl(int p, F &&f) {
     else if (p <= 128) f(std::integral_constant<int, 32>{});
     else {
         set_error("sparse kernels support at most 128 block columns");
+        throw Error{LRA_EINVAL};
+    }
+}
+
+void check_sparse_p(int p) {
+    if (p < 1 || p > 128) {
+        set_error("sparse kernels support 1 to 128 block columns");
         throw Error{LRA_EINVAL};
     }
 }
@@ -817,18 +909,15 @@ void sparse_colnorms(cudaStream_t s, const int64_t *colptr, const float *cval, i
 
 void spmm_xt(cudaStream_t s, const int64_t *colptr, const int32_t *rowidx, const float *cval, int64_t n,
              int64_t d, const float *Wr, int PP, int p, float *Y) {
+    check_sparse_p(p);
     const int p4 = (p + 3) & ~3;
     const int H = (int)std::min<int64_t>(d, (int64_t)(kHotBytes / (sizeof(float) * p4)));
     const size_t smem = sizeof(float) * (size_t)H * p4;
-    dispatch_gl(p, [&](auto glc) {
-        constexpr int GL = decltype(glc)::value;
-        auto k = spmm_xt4_kernel<GL>;
-        ensure_smem(k, (int)std::max<size_t>(smem, 1));
-        const unsigned grid = (unsigned)std::max<int64_t>(
-            1, std::min<int64_t>((int64_t)sm_count_sparse() * kXtPerSm, ceil_div(n, kXtThreads / 32)));
-        k<<<grid, kXtThreads, smem, s>>>(colptr, rowidx, cval, n, Wr, PP, p, H, Y);
-        LRA_LAUNCHED();
-    });
+    ensure_smem(spmm_xt_kernel, (int)std::max<size_t>(smem, 1));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sm_count_sparse() * kXtPerSm, ceil_div(n, kXtThreads / 32)));
+    spmm_xt_kernel<<<grid, kXtThreads, smem, s>>>(colptr, rowidx, cval, n, Wr, PP, p, H, Y);
+    LRA_LAUNCHED();
 }
 
 void spmm_x(cudaStream_t s, const int64_t *rowptr, const int32_t *colidx, const float *val, int64_t d,

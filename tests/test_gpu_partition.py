@@ -97,13 +97,13 @@ def test_partition_on_csr_input(ctx):
         lra.lra_mat_destroy(m)
 
 
-def test_partition_on_csr_input_beyond_the_dense_inner_limit(ctx):
-    """d = 20000, above the dense inner loop's reach: the deflated stages step
-    in the CSR kernels' factored form with the projection applied on the fly (no
-    d x n copy of the deflated matrix is formed).  lambda_1 is far above lambda_2 (a
+def test_partition_on_csr_input_in_factored_steps(ctx):
+    """d = 12000, above the d up to which deflated CSR columns are formed
+    densely: the deflated stages step in the CSR kernels' factored form with
+    the projection applied on the fly (no d x n copy of the deflated matrix).  lambda_1 is far above lambda_2 (a
     multiplicative gap at 1), so a second, deflated stage follows the first."""
-    d, n, k, p = 20000, 6000, 3, 6
-    rowptr, colidx, val = L.zipf_csr(d, n, 43, mean_nnz=20.0)
+    d, n, k, p = 12000, 3000, 3, 6
+    rowptr, colidx, val = L.zipf_csr(d, n, 43, mean_nnz=15.0)
     Xs = sp.csr_matrix((val, colidx, rowptr), shape=(d, n)).T.tocsr()
     lam = O.top_eigs_lanczos(Xs, p + 1)
     assert lam[1] < lam[0] * (1 - 1.0 / p ** 2)
