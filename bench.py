@@ -297,7 +297,8 @@ class DenseSource:
         self.wl, self.lra, self.args = wl, lra, args
         self.storage = {"f32": lra.LRA_F32, "bf16": lra.LRA_BF16, "f16": lra.LRA_F16}[args.storage]
         self.esize = 4 if args.storage == "f32" else 2
-        self.Xt, _ = L.planted_torch(wl.d, wl.n, wl.sigma(), wl.seed, device=device)
+        self.Xt, Uplant = L.planted_torch(wl.d, wl.n, wl.sigma(), wl.seed, device=device)
+        self.Uk = np.ascontiguousarray(Uplant[:, :wl.k])  # the planted top-k directions
         torch.cuda.synchronize()
         self.x_bytes = wl.d * wl.n * self.esize
         self.h2d_bytes = wl.d * wl.n * 4
@@ -337,6 +338,13 @@ class DenseSource:
             del blk, P
         torch.cuda.empty_cache()
         return tot - proj
+
+    def sin_k(self, U):
+        """sin of the largest principal angle between span(U) (k rows) and the
+        planted U_k (FP64)."""
+        Ug = np.linalg.qr(U.double().cpu().numpy().T)[0]
+        s = np.linalg.svd(self.Uk.T @ Ug, compute_uv=False)
+        return float(np.sqrt(max(0.0, 1.0 - float(s.min()) ** 2)))
 
     def pass_bytes(self, kind, pav, storage=None):
         esize = self.esize if storage is None else (4 if storage == "f32" else 2)
@@ -613,6 +621,7 @@ def run_lra(args):
     # accuracy of the last solve, off the clock (FP64 error against the
     # closed-form or stored reference optimum)
     ratio = src.err(U) / opt_val
+    sin_k = src.sin_k(U) if hasattr(src, "sin_k") else None
     roof, per_kernel, tot = kernel_table(reps, src, args.storage, wl, peaks, peak_kind, args.workload)
     lra.lra_mat_destroy(mat)
     mat = None
@@ -705,7 +714,7 @@ def run_lra(args):
                        "acc": bool(args.acc), "partition": bool(args.partition),
                        "l2": "inputs larger than L2 (X %.2f GB per pass)" % (src.x_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "accuracy": {"ratio_err_over_opt": ratio, "outer_iters": last.outer_iters,
+            "accuracy": {"ratio_err_over_opt": ratio, "sin_vs_planted_uk": sin_k, "outer_iters": last.outer_iters,
                          "status": reps[-1][0]},
             "partition_stages": ([[int(last.part_q[t]), "power" if last.part_kind[t] == 1 else "shift"]
                                   for t in range(last.part_stages)] if args.partition else None),

@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
 
     for (int e = tid; e < 3 * NV * 16; e += NT) (&red[0][0][0])[e] = 0.0f;
 
-    // Delta = W - Wt and eta M, rows 4 (t + s NT) + {0, 1} and + {2, 3} as pairs
+    // Delta = W - Wt and -eta M, rows 4 (t + s NT) + {0, 1} and + {2, 3} as pairs
+    // (-eta M is kept negated, so every update is two packed FMAs)
     float2 dl[S][2][PC];
     float2 mm[S][2][PC];
 #pragma unroll
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
             for (int h = 0; h < 2; ++h) {
                 dl[s][h][j] = ok ? make_float2(W[off + 2 * h] - Wt[off + 2 * h], W[off + 2 * h + 1] - Wt[off + 2 * h + 1])
                                  : make_float2(0.0f, 0.0f);
-                mm[s][h][j] = ok ? make_float2(eta * M[off + 2 * h], eta * M[off + 2 * h + 1]) : make_float2(0.0f, 0.0f);
+                mm[s][h][j] = ok ? make_float2(-eta * M[off + 2 * h], -eta * M[off + 2 * h + 1]) : make_float2(0.0f, 0.0f);
             }
         }
     }
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
             }
         }
     };
-    // partial sums of y^T Delta and y^T (eta M) per column, and y^T z
+    // partial sums of y^T Delta and y^T (-eta M) per column, and y^T z
     auto dots = [&](const float2 (&y)[S][2], const float2 (&z)[S][2], float *u, float *w, float &vv) {
 #pragma unroll
         for (int j = 0; j < PC; ++j) {
@@ -522,10 +523,8 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int j = 0; j < PC; ++j) {
-                    const float2 nm = make_float2(-mm[s][h][j].x, -mm[s][h][j].y);
-                    dl[s][h][j] = ffma2(a2v, dl[s][h][j], ffma2(make_float2(c[j], c[j]), x[s][h], nm));
-                }
+                for (int j = 0; j < PC; ++j)
+                    dl[s][h][j] = ffma2(a2v, dl[s][h][j], ffma2(make_float2(c[j], c[j]), x[s][h], mm[s][h][j]));
     };
 
 #pragma unroll
@@ -583,13 +582,13 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
         block_sum16<NV, NP, NW>(acc, redb, lane, warp);
         float c1[PC];
 #pragma unroll
-        for (int j = 0; j < PC; ++j) c1[j] = c1v * fmaf(a, acc[j], fmaf(ct[j], acc[4 * PC], -acc[PC + j]));
+        for (int j = 0; j < PC; ++j) c1[j] = c1v * fmaf(a, acc[j], fmaf(ct[j], acc[4 * PC], acc[PC + j]));
         if (t + 1 < m) {
             // step t + 1
             update(xb, c1);
 #pragma unroll
             for (int j = 0; j < PC; ++j)
-                r[j] = fmaf(a, acc[2 * PC + j], fmaf(c1[j], acc[4 * PC + 1], -acc[3 * PC + j]));
+                r[j] = fmaf(a, acc[2 * PC + j], fmaf(c1[j], acc[4 * PC + 1], acc[3 * PC + j]));
         }
     };
     for (int64_t t = 0; t < m; t += 4) {
