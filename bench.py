@@ -339,11 +339,13 @@ class DenseSource:
         torch.cuda.empty_cache()
         return tot - proj
 
-    def sin_k(self, U):
-        """sin of the largest principal angle between span(U) (k rows) and the
-        planted U_k (FP64)."""
-        Ug = np.linalg.qr(U.double().cpu().numpy().T)[0]
-        s = np.linalg.svd(self.Uk.T @ Ug, compute_uv=False)
+    def sin_k(self, U, h=None):
+        """sin of the largest principal angle between the span of U's first h
+        rows (all k when h is None; rows in Ritz-value order) and the planted
+        top-h directions (FP64)."""
+        h = self.Uk.shape[1] if h is None else min(h, self.Uk.shape[1])
+        Ug = np.linalg.qr(U[:h].double().cpu().numpy().T)[0]
+        s = np.linalg.svd(self.Uk[:, :h].T @ Ug, compute_uv=False)
         return float(np.sqrt(max(0.0, 1.0 - float(s.min()) ** 2)))
 
     def pass_bytes(self, kind, pav, storage=None):
@@ -622,6 +624,7 @@ def run_lra(args):
     # closed-form or stored reference optimum)
     ratio = src.err(U) / opt_val
     sin_k = src.sin_k(U) if hasattr(src, "sin_k") else None
+    sin_10 = src.sin_k(U, 10) if hasattr(src, "sin_k") else None
     roof, per_kernel, tot = kernel_table(reps, src, args.storage, wl, peaks, peak_kind, args.workload)
     lra.lra_mat_destroy(mat)
     mat = None
@@ -714,7 +717,8 @@ def run_lra(args):
                        "acc": bool(args.acc), "partition": bool(args.partition),
                        "l2": "inputs larger than L2 (X %.2f GB per pass)" % (src.x_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "accuracy": {"ratio_err_over_opt": ratio, "sin_vs_planted_uk": sin_k, "outer_iters": last.outer_iters,
+            "accuracy": {"ratio_err_over_opt": ratio, "sin_vs_planted_uk": sin_k,
+                         "sin_vs_planted_u10": sin_10, "outer_iters": last.outer_iters,
                          "status": reps[-1][0]},
             "partition_stages": ([[int(last.part_q[t]), "power" if last.part_kind[t] == 1 else "shift"]
                                   for t in range(last.part_stages)] if args.partition else None),

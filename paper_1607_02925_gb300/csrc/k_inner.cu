@@ -440,6 +440,8 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
     constexpr int BYTES = 4 * sizeof(TX);
 
     for (int e = tid; e < 3 * NV * 16; e += NT) (&red[0][0][0])[e] = 0.0f;
+    // every zero lands before any warp writes its first partial sum
+    __syncthreads();
 
     // Delta = W - Wt and -eta M, rows 4 (t + s NT) + {0, 1} and + {2, 3} as pairs
     // (-eta M is kept negated, so every update is two packed FMAs)

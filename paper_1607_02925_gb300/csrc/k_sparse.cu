@@ -325,15 +325,17 @@ __device__ __forceinline__ float4 gather_line4(const int32_t *__restrict__ idx, 
     const int g = lane / GL, l = lane % GL;
     const bool colok = 4 * l < p;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    // the (index, value) chunk of 32 entries is loaded one chunk ahead
-    int32_t rn = lo + lane < hi ? __ldg(idx + lo + lane) : 0;
-    float vn = lo + lane < hi ? __ldg(vals + lo + lane) : 0.0f;
+    // the (index, value) chunk of 32 entries is loaded one chunk ahead, with the
+    // streaming (evict-first) hint: each entry is read once per pass, and the
+    // gathered rows of B should keep the L2 lines
+    int32_t rn = lo + lane < hi ? __ldcs(idx + lo + lane) : 0;
+    float vn = lo + lane < hi ? __ldcs(vals + lo + lane) : 0.0f;
     for (int64_t base = lo; base < hi; base += 32) {
         const int32_t rr = rn;
         const float vv = vn;
         const int64_t k = base + 32 + lane;
-        rn = k < hi ? __ldg(idx + k) : 0;
-        vn = k < hi ? __ldg(vals + k) : 0.0f;
+        rn = k < hi ? __ldcs(idx + k) : 0;
+        vn = k < hi ? __ldcs(vals + k) : 0.0f;
         const int cnt = (int)((hi - base) < 32 ? (hi - base) : 32);
 #pragma unroll 4
         for (int e = 0; e < cnt; e += NG) {
