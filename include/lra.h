@@ -117,9 +117,10 @@ typedef struct lra_options {
                                in lra_solve_info.status, the iterate is kept) */
     int64_t acc_target;     /* samples per epoch the proximal weight aims for; 0 = n */
     int partition;          /* 1: Algorithm 6 in full (Sec. 3): adaptive partitioning of {1..k}
-                               with deflation.  Stage t at index s forms X_{-(s-1)} =
-                               (I - U U^T) X explicitly (dense, the original storage; FP32 for
-                               a CSR X), runs Algorithm 3 on A_{-(s-1)} (eps' = 1/(9 p^2)) and
+                               with deflation.  Stage t at index s works on X_{-(s-1)} =
+                               (I - U U^T) X applied on the fly (projected X passes, sampling
+                               by ||x_i||^2 - ||U^T x_i||^2, inner steps on x_i - U U^T x_i; no
+                               copy of X), runs Algorithm 3 on A_{-(s-1)} (eps' = 1/(9 p^2)) and
                                Algorithm 4; a multiplicative gap gives Algorithm 1 on A with
                                q - s + 1 columns, otherwise Algorithm 7, Algorithm 3 on
                                D_{-(s-1)} (eps' = 1/(9p)), Algorithm 5 and Algorithm 1 on D
@@ -251,7 +252,8 @@ lra_status lra_solve(lra_mat *mat, int k, int p, double eps, uint64_t seed, cons
 lra_status lra_submit(lra_ctx *ctx, lra_mat *mat, int k, int p, double eps, uint64_t seed,
                       const lra_options *opt, lra_job *out);
 /* (options.partition = 1 gives LRA_EUNSUPPORTED here: its stages allocate
- * deflated copies of X that a fixed admission footprint does not cover.) */
+ * per-stage buffers (U^T X, deflated sampling tables, the inner loop's deflated
+ * columns) that a fixed admission footprint does not cover.) */
 
 /* Wait up to timeout_ms (0 = do not wait, < 0 = forever) for a job.  On
  * completion copies U/ritz/report (each may be NULL) as lra_solve would, frees

@@ -281,8 +281,9 @@ lra_status lra_submit(lra_ctx *ctx, lra_mat *mat, int k, int p, double eps, uint
     try {
         const Opts o = read_opts(opt, mat->storage);
         if (o.partition) {
-            // Algorithm 6's stages allocate deflated copies of X as they go, which
-            // admission by a fixed footprint cannot account for
+            // Algorithm 6's stages allocate their deflation buffers (U^T X, the
+            // deflated sampling tables, the inner loop's deflated columns) as they
+            // go, which admission by a fixed footprint does not account for
             set_error("the request loop runs the q = k path; partition = 1 needs lra_solve");
             return LRA_EUNSUPPORTED;
         }
