@@ -5,7 +5,8 @@ the deflation on the fly; the oracle forms the deflated matrix.
 The stage decisions (which q each stage finds, and by which branch) are
 integers taken from estimates with wide margins on the planted workload, so
 they must equal the oracle's; the answer must meet the ratio 1 + eps against
-the planted optimum and span the oracle's subspace (sin angle <= 1e-3).
+the planted optimum and span the oracle's subspace (sin angle <= 2e-5 with FP32
+X, <= 3e-3 with BF16 X passes).
 """
 import ctypes
 
@@ -67,8 +68,11 @@ def test_partition_matches_oracle(ctx, planted, storage):
         assert stages(rep) == [(1, 1), (2, 2), (3, 2)]
         ratio = O.frobenius_error(Xt, cm(Ud)) / wl.opt()
         assert 1.0 - 1e-6 <= ratio <= 1.0 + 1e-3
-        assert O.sin_angle(cm(Ud), ref.U) < (1e-3 if storage == "f32" else 1e-2)
-        assert np.allclose(ritz.cpu().numpy(), ref.ritz, rtol=1e-5)
+        # FP32: the same stages, iteration counts and samples as the oracle, so the
+        # two runs agree to FP32 rounding (measured sin 3.3e-6, Ritz values 4e-8);
+        # BF16 X passes: measured sin 9e-4
+        assert O.sin_angle(cm(Ud), ref.U) < (2e-5 if storage == "f32" else 3e-3)
+        assert np.allclose(ritz.cpu().numpy(), ref.ritz, rtol=(1e-6 if storage == "f32" else 1e-5))
     finally:
         lra.lra_mat_destroy(m)
 
