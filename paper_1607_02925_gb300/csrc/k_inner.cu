@@ -440,7 +440,19 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
     constexpr int BYTES = 4 * sizeof(TX);
 
     for (int e = tid; e < 3 * NV * 16; e += NT) (&red[0][0][0])[e] = 0.0f;
-    // every zero lands before any warp writes its first partial sum
+    // the sample indices and weights in windows of 128 steps, two in shared memory:
+    // window w in slot w & 1, window w + 1 fetched while w runs (NT >= 128 here)
+    __shared__ int32_t sidx[2][128];
+    __shared__ float scv[2][128];
+    if (tid < 128) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t u = (int64_t)h * 128 + tid;
+            sidx[h][tid] = u < m ? idx[u] : 0;
+            scv[h][tid] = u < m ? cval[u] : 0.0f;
+        }
+    }
+    // every zero and window entry lands before any warp reads it
     __syncthreads();
 
     // Delta = W - Wt and -eta M, rows 4 (t + s NT) + {0, 1} and + {2, 3} as pairs
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
     for (int s = 0; s < S; ++s) rofs[s] = 4 * (tid + s * NT);
     auto prefetch = [&](int64_t t, int slot) {
         if (t < m) {
-            const TX *col = X + (int64_t)idx[t] * ldx;
+            const TX *col = X + (int64_t)sidx[(t >> 7) & 1][t & 127] * ldx;
             TX *dst = ring + slot * dp;
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -554,6 +566,8 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
         for (int j = 0; j < PC; ++j) r[j] = v0[j];
     }
     int s0 = 0;  // t mod R
+    int32_t pidx = 0;  // the next window's entry of this thread, between load and store
+    float pcv = 0.0f;
     // two steps from column t in xa (columns t + 1, t + 2 loaded into xb, xc);
     // the loop alternates the roles of x0 and x2 instead of copying x2 to x0
     auto two_steps = [&](int64_t t, float2 (&xa)[S][2], float2 (&xb)[S][2], float2 (&xc)[S][2],
@@ -567,8 +581,22 @@ __global__ void __launch_bounds__(32 * NW) svrg_inner_la_kernel(
         load(t + 1, sp1, xb);
         load(t + 2, sp2, xc);
         s0 = sp2;
-        const float c0 = etac * cval[t];
-        const float c1v = (t + 1 < m) ? etac * cval[t + 1] : 0.0f;
+        // window (t / 128) + 1: loaded into registers at t = 0 mod 128 and stored
+        // two steps later; its slot last served window t / 128 - 1, whose final
+        // reads came before the previous block barrier, and its first reads come
+        // ~60 barriers later
+        if ((t & 127) == 0) {
+            const int64_t u = t + 128 + tid;
+            if (tid < 128) {
+                pidx = u < m ? idx[u] : 0;
+                pcv = u < m ? cval[u] : 0.0f;
+            }
+        } else if ((t & 127) == 2 && tid < 128) {
+            sidx[((t >> 7) + 1) & 1][tid] = pidx;
+            scv[((t >> 7) + 1) & 1][tid] = pcv;
+        }
+        const float c0 = etac * scv[(t >> 7) & 1][t & 127];
+        const float c1v = (t + 1 < m) ? etac * scv[((t + 1) >> 7) & 1][(t + 1) & 127] : 0.0f;
         float ct[PC];
 #pragma unroll
         for (int j = 0; j < PC; ++j) ct[j] = c0 * r[j];
