@@ -549,7 +549,10 @@ lra_status Engine::cholqr2(float *W, int p, bool deferred) {
     LRA_CUDA(cudaMemsetAsync(ws_.status, 0, sizeof(int) * 2, s_));
     for (int pass = 0; pass < 2; ++pass) {
         gram(s_, W, dpad, 1, dpad, p, ws_.Gm, ws_.gscr);
-        chol(s_, ws_.Gm, p, ws_.Rinv, ws_.status + pass);
+        // the second pass's Gram is I + E with E at the first pass's rounding
+        // level for a well-conditioned block: its Cholesky factor to first order
+        // (error below 1e-9) replaces the FP64 factorisation there
+        chol(s_, ws_.Gm, p, ws_.Rinv, ws_.status + pass, pass == 1 ? 3e-5 : 0.0);
         trsm_rows(s_, W, dpad, dpad, p, ws_.Rinv, ws_.T1);
         LRA_CUDA(cudaMemcpyAsync(W, ws_.T1, sizeof(float) * dpad * p, cudaMemcpyDeviceToDevice, s_));
     }

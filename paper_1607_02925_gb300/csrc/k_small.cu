@@ -290,14 +290,39 @@ int gram_blocks(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_
 // R = L^T (upper, FP32 row-major); status = 1 if a pivot is not positive.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) chol_kernel(const double *__restrict__ G, int p,
-                                                   float *__restrict__ R, int *__restrict__ status) {
+                                                   float *__restrict__ R, int *__restrict__ status,
+                                                   double near_id) {
     extern __shared__ __align__(16) double sl[];
     const int ld = p + 1;
     double *L = sl;               // [p][ld]
     double *piv = sl + p * ld;    // [p]
     double *g0 = piv + p;         // [p] original diagonal
     __shared__ int bad;
+    __shared__ double wsum[8];
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (near_id > 0.0) {
+        // G = I + E with ||E||_F <= near_id: R = I + F, F upper with F + F^T = E
+        // to first order (F = triu(E, 1) + diag(E) / 2); the dropped F^T F is
+        // below near_id^2 in norm
+        double e2 = 0.0;
+        for (int e = tid; e < p * p; e += nt) {
+            const double v = G[e] - ((e % p) == (e / p) ? 1.0 : 0.0);
+            e2 = fma(v, v, e2);
+        }
+        e2 = warp_sum(e2);
+        if ((tid & 31) == 0) wsum[tid >> 5] = e2;
+        __syncthreads();
+        double tot = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) tot += wsum[w];
+        if (sqrt(tot) <= near_id) {
+            for (int e = tid; e < p * p; e += nt) {
+                const int a = e / p, b = e % p;  // R[a][b], G column-major
+                R[e] = b > a ? (float)G[a + (int64_t)b * p] : (b == a ? (float)(0.5 * (1.0 + G[e])) : 0.0f);
+            }
+            if (tid == 0) *status = 0;
+            return;
+        }
+    }
     if (tid == 0) bad = 0;
     for (int e = tid; e < p * p; e += nt) L[(e % p) * ld + e / p] = G[e];
     for (int c = tid; c < p; c += nt) g0[c] = G[c + (int64_t)c * p];
@@ -802,11 +827,11 @@ void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, doub
     LRA_LAUNCHED();
 }
 
-void chol(cudaStream_t s, const double *G, int p, float *R, int *status) {
+void chol(cudaStream_t s, const double *G, int p, float *R, int *status, double near_id) {
     const size_t smem = sizeof(double) * ((size_t)p * (p + 1) + 2 * p);
     ensure_smem(chol_kernel, (int)smem);
     const int nt = p <= 48 ? 128 : 256;
-    chol_kernel<<<1, nt, smem, s>>>(G, p, R, status);
+    chol_kernel<<<1, nt, smem, s>>>(G, p, R, status, near_id);
     LRA_LAUNCHED();
 }
 

@@ -116,7 +116,9 @@ void cross_full(cudaStream_t s, const float *A, const float *B, int64_t rows, in
 // to first order in G - I (all p x p FP64 column-major, symmetric)
 void ortho_correct(cudaStream_t s, const double *H, const double *G, int p, double *Hc);
 // Cholesky G = R^T R in FP64 (one barrier per column); R upper FP32 row-major
-void chol(cudaStream_t s, const double *G, int p, float *R, int *status);
+// near_id > 0: when ||G - I||_F <= near_id, R is the first-order factor
+// I + triu(G - I, 1) + diag(G - I) / 2 (error below near_id^2) instead
+void chol(cudaStream_t s, const double *G, int p, float *R, int *status, double near_id = 0.0);
 // Q = W R^-1 by row-wise forward substitution (W, Q rows x p column-major)
 void trsm_rows(cudaStream_t s, const float *W, int64_t rows, int64_t ld, int p, const float *R, float *Q);
 // Out (rows x q) = A (rows x p) T (p x q, FP32 row-major); strides for A and Out
