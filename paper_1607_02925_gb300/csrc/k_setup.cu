@@ -365,47 +365,66 @@ __device__ __forceinline__ float load_f32(const TS *p) { return to_f32(*p); }
 template <>
 __device__ __forceinline__ float load_f32<double>(const double *p) { return __double2float_rn(*p); }
 
+// Column-major conversion: CTA per column (grid-stride over columns), threads
+// along the rows, no per-element division; rows d..dpad-1 are written as zeros.
+// An FP32 source with 16-byte aligned columns (ld a multiple of 4) moves as float4.
 template <typename TS, typename TD>
-__global__ void convert_kernel(const TS *__restrict__ src, int64_t ld, int64_t d, int64_t ncols,
-                               TD *__restrict__ dst, int64_t dpad) {
-    const int64_t total = dpad * ncols;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e % dpad, col = e / dpad;
-        float v = 0.0f;
-        TD out;
-        if (r < d) {
-            if constexpr (sizeof(TS) == 8 && sizeof(TD) == 2) {
-                out = __double2bfloat16(*reinterpret_cast<const double *>(src + r + col * ld));
-                dst[e] = out;
+__global__ void __launch_bounds__(256) convert_kernel(const TS *__restrict__ src, int64_t ld, int64_t d,
+                                                      int64_t ncols, TD *__restrict__ dst, int64_t dpad,
+                                                      bool vec4) {
+    for (int64_t col = blockIdx.x; col < ncols; col += gridDim.x) {
+        const TS *sc = src + col * ld;
+        TD *dc = dst + col * dpad;
+        if constexpr (sizeof(TS) == 4 && sizeof(TD) == 4) {
+            if (vec4) {
+                const int64_t d4 = d >> 2;
+                for (int64_t q = threadIdx.x; q < (dpad >> 2); q += blockDim.x) {
+                    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (q < d4) {
+                        v = reinterpret_cast<const float4 *>(sc)[q];
+                    } else if (4 * q < d) {
+                        const int64_t r = 4 * q;
+                        v.x = sc[r];
+                        if (r + 1 < d) v.y = sc[r + 1];
+                        if (r + 2 < d) v.z = sc[r + 2];
+                    }
+                    reinterpret_cast<float4 *>(dc)[q] = v;
+                }
                 continue;
-            } else {
-                v = load_f32(src + r + col * ld);
             }
         }
-        if constexpr (sizeof(TD) == 2)
-            out = __float2bfloat16_rn(v);
-        else
-            out = v;
-        dst[e] = out;
+        for (int64_t r = threadIdx.x; r < dpad; r += blockDim.x) {
+            TD out;
+            if constexpr (sizeof(TS) == 8 && sizeof(TD) == 2) {
+                out = r < d ? __double2bfloat16(sc[r]) : __float2bfloat16_rn(0.0f);
+            } else {
+                const float v = r < d ? load_f32(sc + r) : 0.0f;
+                if constexpr (sizeof(TD) == 2)
+                    out = __float2bfloat16_rn(v);
+                else
+                    out = v;
+            }
+            dc[r] = out;
+        }
     }
 }
 
 template <typename TD>
 static void convert_dispatch(cudaStream_t s, const void *src, lra_dtype sdt, int64_t ld, int64_t d,
                              int64_t ncols, TD *dst, int64_t dpad) {
-    const int64_t total = dpad * ncols;
-    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 64);
+    if (ncols <= 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>(ncols, 152 * 16);
+    const bool vec4 = sdt == LRA_F32 && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
     switch (sdt) {
         case LRA_F32:
-            convert_kernel<float, TD><<<blocks, 256, 0, s>>>((const float *)src, ld, d, ncols, dst, dpad);
+            convert_kernel<float, TD><<<blocks, 256, 0, s>>>((const float *)src, ld, d, ncols, dst, dpad, vec4);
             break;
         case LRA_BF16:
             convert_kernel<__nv_bfloat16, TD><<<blocks, 256, 0, s>>>((const __nv_bfloat16 *)src, ld, d,
-                                                                    ncols, dst, dpad);
+                                                                    ncols, dst, dpad, false);
             break;
         case LRA_F64:
-            convert_kernel<double, TD><<<blocks, 256, 0, s>>>((const double *)src, ld, d, ncols, dst, dpad);
+            convert_kernel<double, TD><<<blocks, 256, 0, s>>>((const double *)src, ld, d, ncols, dst, dpad, false);
             break;
         default:
             set_error("unsupported source dtype");
