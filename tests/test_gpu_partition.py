@@ -127,6 +127,39 @@ def test_partition_on_csr_input_in_factored_steps(ctx):
         lra.lra_mat_destroy(m)
 
 
+@pytest.mark.parametrize("kind", ["dense", "csr_factored"])
+def test_partition_with_minibatch_steps(ctx, kind):
+    """Minibatch inner steps (b = 2) inside the deflated stages: dense X steps on
+    the formed deflated columns, a CSR X with d > 8192 in the batched factored
+    form; the answer meets the ratio against the optimum."""
+    if kind == "dense":
+        wl = L.WORKLOADS["partition_64x800"]
+        Xt, U, s = L.planted_numpy(wl.d, wl.n, wl.sigma(), wl.seed)
+        X32 = np.ascontiguousarray(Xt.astype(np.float32))
+        d, n, k, p, opt_val, Xref = wl.d, wl.n, wl.k, wl.p, wl.opt(), Xt
+        m = lra.lra_create_dense(ctx, d, n, lra.LRA_F32, X32, d, False, lra.LRA_F32)
+        o = lra.options(partition=1, delta=0.5, acc=1, batch=2)
+    else:
+        d, n, k, p = 9000, 2000, 3, 6
+        rowptr, colidx, val = L.zipf_csr(d, n, 47, mean_nnz=10.0)
+        Xref = sp.csr_matrix((val, colidx, rowptr), shape=(d, n)).T.tocsr()
+        lam = O.top_eigs_lanczos(Xref, p + 1)
+        opt_val = O.colnorms(Xref)[1] - float(lam[:k].sum())
+        m = lra.lra_create_csr(ctx, d, n, int(rowptr[-1]), rowptr, colidx, val, False)
+        o = lra.options(partition=1, acc=1, batch=2, part_max_iters=30)
+    try:
+        Ud = torch.zeros(k, d, dtype=torch.float32, device=DEV)
+        ritz = torch.zeros(k, dtype=torch.float64, device=DEV)
+        rep = lra.LraReport()
+        st = lra.lra_solve(m, k, p, 1e-3, 5, o, Ud, ritz, rep)
+        assert st == 0
+        assert rep.part_stages >= 2
+        ratio = O.frobenius_error(Xref, cm(Ud)) / opt_val
+        assert 1.0 - 1e-6 <= ratio <= 1.0 + 1e-3
+    finally:
+        lra.lra_mat_destroy(m)
+
+
 def test_partition_option_errors(ctx):
     wl = L.WORKLOADS["partition_64x800"]
     Xt, U, s = L.planted_numpy(wl.d, wl.n, wl.sigma(), wl.seed)
